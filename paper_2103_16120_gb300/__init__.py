@@ -1,0 +1,172 @@
+"""GB300-native elliptic solver for the semi-implicit shallow-water model on
+the longitude/latitude sphere (preconditioned GCR(k), Sec. 2.3).
+
+Thin Python binding of the C ABI (include/sw_elliptic.h): the functions keep
+the ABI's names and only marshal arguments -- torch CUDA tensors become device
+pointers, the current torch stream becomes the CUDA stream.  Every step of the
+solve runs in the library's CUDA kernels; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from typing import Sequence
+
+from ._lib import (  # noqa: F401
+    EXPORTS, SolveOpts, SolveStats, STATUS_NAMES, load,
+    SW_OK, SW_ERR_INVALID_ARG, SW_ERR_CUDA, SW_ERR_OOM, SW_ERR_NOT_CONVERGED, SW_ERR_BREAKDOWN,
+    SW_ERR_NONFINITE, SW_ERR_TIMEOUT, SW_ERR_INTERNAL,
+    SW_PREC_FP64, SW_PREC_MIXED_FP16, SW_PREC_MIXED_BF16, SW_PREC_FP32,
+    SW_PC_NONE, SW_PC_DIAG, SW_PC_DIAG_RICHARDSON, SW_PC_SI_RICHARDSON,
+)
+
+COEFF_KEYS = ("A11", "A12", "A21", "A22", "B1", "B2", "C")
+# outcomes of a solve that are reported in the stats rather than raised
+SOLVE_OUTCOMES = (SW_OK, SW_ERR_NOT_CONVERGED, SW_ERR_BREAKDOWN, SW_ERR_NONFINITE)
+
+
+class SwError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        msg = load().sw_last_error().decode(errors="replace")
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _check(status: int, where: str, allowed=(SW_OK,)):
+    if status not in allowed:
+        raise SwError(status, where)
+    return status
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t, dtype=None, shape=None):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"expected dtype {dtype}, got {t.dtype}")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"expected shape {tuple(shape)}, got {tuple(t.shape)}")
+    return C.c_void_p(t.data_ptr())
+
+
+def sw_solve_opts_default(**overrides) -> SolveOpts:
+    o = SolveOpts()
+    load().sw_solve_opts_default(C.byref(o))
+    for k, v in overrides.items():
+        if not hasattr(o, k):
+            raise AttributeError(k)
+        if k in ("res_history", "row_residual") and v is not None and not isinstance(v, int):
+            v = v.data_ptr()
+        setattr(o, k, v)
+    return o
+
+
+class Grid:
+    """Handle of an nx x ny grid (sw_grid); destroyed with the object."""
+
+    def __init__(self, nx: int, ny: int, radius: float = 6.371e6):
+        h = C.c_void_p()
+        _check(load().sw_grid_create(int(nx), int(ny), float(radius), C.byref(h)), "sw_grid_create")
+        self.handle = h
+        self.nx, self.ny = int(nx), int(ny)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            try:
+                load().sw_grid_destroy(h)
+            except Exception:
+                pass
+            self.handle = None
+
+
+def sw_grid_create(nx: int, ny: int, radius: float = 6.371e6) -> Grid:
+    return Grid(nx, ny, radius)
+
+
+def sw_grid_destroy(g: Grid) -> None:
+    if g.handle is not None and g.handle.value:
+        _check(load().sw_grid_destroy(g.handle), "sw_grid_destroy")
+        g.handle = None
+
+
+def sw_grid_workspace_bytes(g: Grid, opts: SolveOpts | None = None) -> int:
+    n = C.c_size_t()
+    _check(load().sw_grid_workspace_bytes(g.handle, C.byref(opts) if opts else None, C.byref(n)),
+           "sw_grid_workspace_bytes")
+    return n.value
+
+
+def sw_grid_attach_workspace(g: Grid, buf) -> None:
+    ptr = None if buf is None else C.c_void_p(buf.data_ptr())
+    nbytes = 0 if buf is None else buf.numel() * buf.element_size()
+    _check(load().sw_grid_attach_workspace(g.handle, ptr, nbytes), "sw_grid_attach_workspace")
+
+
+def sw_elliptic_set_coeffs(g: Grid, A11, A12, A21, A22, B1, B2, C_, stream=None) -> None:
+    import torch
+    shp = (g.ny, g.nx)
+    ptrs = [_ptr(t, torch.float64, shp) for t in (A11, A12, A21, A22, B1, B2, C_)]
+    _check(load().sw_elliptic_set_coeffs(g.handle, *ptrs, _stream(stream)), "sw_elliptic_set_coeffs")
+
+
+def sw_grid_set_eta(g: Grid, eta: float, stream=None) -> None:
+    _check(load().sw_grid_set_eta(g.handle, float(eta), _stream(stream)), "sw_grid_set_eta")
+
+
+def sw_grid_get_eta(g: Grid) -> float:
+    v = C.c_double()
+    _check(load().sw_grid_get_eta(g.handle, C.byref(v)), "sw_grid_get_eta")
+    return v.value
+
+
+def sw_operator_apply(g: Grid, x, y, stream=None) -> None:
+    """y = L(x); FP64 for float64 tensors, FP32 for float32 tensors."""
+    import torch
+    prec = SW_PREC_FP64 if x.dtype == torch.float64 else SW_PREC_FP32
+    dt = torch.float64 if prec == SW_PREC_FP64 else torch.float32
+    shp = (g.ny, g.nx)
+    _check(load().sw_operator_apply(g.handle, prec, _ptr(x, dt, shp), _ptr(y, dt, shp), _stream(stream)),
+           "sw_operator_apply")
+
+
+def sw_precond_apply(g: Grid, opts: SolveOpts, r, q, stream=None) -> None:
+    import torch
+    dt = torch.float64 if opts.prec == SW_PREC_FP64 else torch.float32
+    shp = (g.ny, g.nx)
+    _check(load().sw_precond_apply(g.handle, C.byref(opts), _ptr(r, dt, shp), _ptr(q, dt, shp), _stream(stream)),
+           "sw_precond_apply")
+
+
+def sw_gcr_solve(g: Grid, opts: SolveOpts, R, phi, stream=None) -> SolveStats:
+    """Solve L(phi) = R in place (phi: first guess in, solution out)."""
+    import torch
+    shp = (g.ny, g.nx)
+    st = SolveStats()
+    _check(load().sw_gcr_solve(g.handle, C.byref(opts), _ptr(R, torch.float64, shp),
+                               _ptr(phi, torch.float64, shp), C.byref(st), _stream(stream)),
+           "sw_gcr_solve", SOLVE_OUTCOMES)
+    return st
+
+
+def sw_ensemble_solve(grids: Sequence[Grid], opts: SolveOpts, Rs, phis, stream=None) -> list:
+    import torch
+    n = len(grids)
+    hs = (C.c_void_p * n)(*[g.handle.value for g in grids])
+    rp = (C.c_void_p * n)(*[_ptr(R, torch.float64, (g.ny, g.nx)).value for g, R in zip(grids, Rs)])
+    pp = (C.c_void_p * n)(*[_ptr(p, torch.float64, (g.ny, g.nx)).value for g, p in zip(grids, phis)])
+    stats = (SolveStats * n)()
+    _check(load().sw_ensemble_solve(n, hs, C.byref(opts), rp, pp, stats, _stream(stream)),
+           "sw_ensemble_solve", SOLVE_OUTCOMES)
+    return list(stats)

@@ -1,0 +1,502 @@
+// sw_api.cu -- the C ABI declared in include/sw_elliptic.h: grid handles,
+// coefficient storage, workspace, argument checks and kernel launches.
+#include <string>
+#include <cstring>
+#include <cmath>
+#include <new>
+#include <vector>
+
+#include "../../include/sw_elliptic.h"
+#include "sw_common.cuh"
+#include "sw_internal.h"
+
+using namespace sw;
+
+static thread_local std::string g_err;
+
+static sw_status fail(sw_status st, const std::string &msg)
+{
+    g_err = msg;
+    return st;
+}
+
+static sw_status cuda_fail(cudaError_t e, const char *where)
+{
+    return fail(e == cudaErrorMemoryAllocation ? SW_ERR_OOM : SW_ERR_CUDA,
+                std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                                   \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);        \
+    } while (0)
+
+struct sw_grid_s {
+    int nx, ny, device, sms;
+    double radius, dlam, dphi;
+    size_t N;
+    // coefficient storage (one allocation)
+    void *cmem;
+    double *ax, *cx, *bx, *ay, *cy, *by, *C, *diag, *lf, *invD, *zz, *gam, *ec, *rowmax, *eta;
+    float *wax, *wcx, *wbx, *way, *wcy, *wby, *wC, *wdiag, *lf32, *invD32, *zz32;
+    bool has_coeffs;
+    double eta_explicit;           // > 0 when chosen by sw_grid_set_eta
+    // solver workspace
+    void *ws;
+    size_t ws_bytes;
+    bool ws_owned;
+    SolverBlock *blk;              // device: member state of this grid
+    MemberCtl *h_ctl;              // pinned host copies read after a solve
+    GlobalCtl *h_g;
+    double *h_eta;
+};
+
+static int row_threads(int nx)
+{
+    int t = ((nx / 4 + 31) / 32) * 32;
+    if (t < 64) t = 64;
+    if (t > MAX_THREADS) t = MAX_THREADS;
+    return t;
+}
+
+static size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
+
+extern "C" void sw_solve_opts_default(sw_solve_opts *o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->k = 4;
+    o->tol = 1e-8;
+    o->max_iters = 1000;
+    o->min_iters = 0;
+    o->pc = SW_PC_SI_RICHARDSON;
+    o->n_richardson = 2;
+    o->eta = 0.0;
+    o->omega = 1.0;
+    o->prec = SW_PREC_FP64;
+    o->pole_band_rows = -1;
+    o->ru_every = 0;
+}
+
+extern "C" const char *sw_last_error(void) { return g_err.c_str(); }
+
+extern "C" sw_status sw_grid_create(int nx, int ny, double radius, sw_grid *out)
+{
+    if (!out) return fail(SW_ERR_INVALID_ARG, "sw_grid_create: out is NULL");
+    *out = nullptr;
+    if (nx < 4 || nx > MAX_NX || (nx & 1)) return fail(SW_ERR_INVALID_ARG, "sw_grid_create: nx must be even, 4..4096");
+    if (ny < 2 || ny > 65536) return fail(SW_ERR_INVALID_ARG, "sw_grid_create: ny must be 2..65536");
+    if (!(radius > 0.0) || !std::isfinite(radius)) return fail(SW_ERR_INVALID_ARG, "sw_grid_create: radius must be > 0");
+    sw_grid g = new (std::nothrow) sw_grid_s();
+    if (!g) return fail(SW_ERR_OOM, "sw_grid_create: host allocation failed");
+    g->nx = nx; g->ny = ny; g->radius = radius;
+    g->dlam = 2.0 * M_PI / nx; g->dphi = M_PI / ny;
+    g->N = (size_t)nx * ny;
+    cudaError_t e = cudaGetDevice(&g->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, g->device);
+    size_t N = g->N;
+    size_t bytes = 11 * al(N * 8) + 3 * al((size_t)ny * 8) + al(8) + 11 * al(N * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&g->cmem, bytes);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&g->blk, sizeof(SolverBlock));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&g->h_ctl, sizeof(MemberCtl) + sizeof(GlobalCtl) + 64);
+    if (e != cudaSuccess) {
+        if (g->cmem) cudaFree(g->cmem);
+        if (g->blk) cudaFree(g->blk);
+        delete g;
+        return cuda_fail(e, "sw_grid_create");
+    }
+    g->h_g = (GlobalCtl *)((char *)g->h_ctl + sizeof(MemberCtl));
+    g->h_eta = (double *)((char *)g->h_g + sizeof(GlobalCtl) + 16);
+    char *p = (char *)g->cmem;
+    double **d64[] = {&g->ax, &g->cx, &g->bx, &g->ay, &g->cy, &g->by, &g->C, &g->diag, &g->lf, &g->invD, &g->zz};
+    for (auto q : d64) { *q = (double *)p; p += al(N * 8); }
+    g->gam = (double *)p; p += al((size_t)ny * 8);
+    g->ec = (double *)p; p += al((size_t)ny * 8);
+    g->rowmax = (double *)p; p += al((size_t)ny * 8);
+    g->eta = (double *)p; p += al(8);
+    float **d32[] = {&g->wax, &g->wcx, &g->wbx, &g->way, &g->wcy, &g->wby, &g->wC, &g->wdiag, &g->lf32, &g->invD32, &g->zz32};
+    for (auto q : d32) { *q = (float *)p; p += al(N * 4); }
+    *out = g;
+    return SW_OK;
+}
+
+extern "C" sw_status sw_grid_destroy(sw_grid g)
+{
+    if (!g) return fail(SW_ERR_INVALID_ARG, "sw_grid_destroy: NULL grid");
+    cudaFree(g->cmem);
+    cudaFree(g->blk);
+    if (g->ws_owned && g->ws) cudaFree(g->ws);
+    cudaFreeHost(g->h_ctl);
+    delete g;
+    return SW_OK;
+}
+
+// ---------------------------------------------------------------------------
+// workspace layout
+// ---------------------------------------------------------------------------
+struct WsLayout {
+    size_t r, qa, qb, e, qa32, qb32, e32, qa_s, qb_s, e_s, Le, p, Lp, part, total;
+};
+
+static WsLayout ws_layout(const sw_grid_s *g, int prec, int k)
+{
+    WsLayout L{};
+    size_t N = g->N, ny = g->ny, off = 0;
+    bool mixed = prec != SW_PREC_FP64;
+    size_t v = mixed ? 4 : 8, q = mixed ? 2 : 8;
+    auto take = [&](size_t b) { size_t o = off; off += al(b); return o; };
+    L.r = take(N * v);
+    L.qa = take(N * q); L.qb = take(N * q); L.e = take(N * q);
+    if (mixed) {
+        L.qa32 = take(N * 4); L.qb32 = take(N * 4); L.e32 = take(N * 4);
+        L.qa_s = take(ny * 4); L.qb_s = take(ny * 4); L.e_s = take(ny * 4);
+    }
+    L.Le = take(N * v);
+    L.p = take(N * v * (k + 1));
+    L.Lp = take(N * v * (k + 1));
+    L.part = take(ny * NSLOT * 8);
+    L.total = off;
+    return L;
+}
+
+static sw_status check_opts(const sw_solve_opts *o, bool solve)
+{
+    if (!o) return fail(SW_ERR_INVALID_ARG, "options are NULL");
+    if (o->k < 1 || o->k > KMAX) return fail(SW_ERR_INVALID_ARG, "k must be 1..16");
+    if (o->pc < 0 || o->pc > 3) return fail(SW_ERR_INVALID_ARG, "pc must be 0..3");
+    if ((o->pc == 2 || o->pc == 3) && (o->n_richardson < 1 || o->n_richardson > 16))
+        return fail(SW_ERR_INVALID_ARG, "n_richardson must be 1..16");
+    if (o->prec < 0 || o->prec > 2) return fail(SW_ERR_INVALID_ARG, "prec must be FP64, MIXED_FP16 or MIXED_BF16");
+    if (solve) {
+        if (o->max_iters < 1) return fail(SW_ERR_INVALID_ARG, "max_iters must be >= 1");
+        if (!(o->tol >= 0.0) || !std::isfinite(o->tol)) return fail(SW_ERR_INVALID_ARG, "tol must be finite and >= 0");
+        if (o->ru_every < 0) return fail(SW_ERR_INVALID_ARG, "ru_every must be >= 0");
+    }
+    if (o->pc == 2 && !(std::isfinite(o->omega))) return fail(SW_ERR_INVALID_ARG, "omega must be finite");
+    if (!std::isfinite(o->eta)) return fail(SW_ERR_INVALID_ARG, "eta must be finite");
+    return SW_OK;
+}
+
+extern "C" sw_status sw_grid_workspace_bytes(sw_grid g, const sw_solve_opts *o, size_t *bytes)
+{
+    if (!g || !bytes) return fail(SW_ERR_INVALID_ARG, "sw_grid_workspace_bytes: NULL argument");
+    sw_solve_opts d;
+    if (!o) { sw_solve_opts_default(&d); o = &d; }
+    sw_status st = check_opts(o, false);
+    if (st) return st;
+    *bytes = ws_layout(g, o->prec, o->k).total;
+    return SW_OK;
+}
+
+extern "C" sw_status sw_grid_attach_workspace(sw_grid g, void *dev_ptr, size_t bytes)
+{
+    if (!g) return fail(SW_ERR_INVALID_ARG, "sw_grid_attach_workspace: NULL grid");
+    if (dev_ptr && ((uintptr_t)dev_ptr & 255)) return fail(SW_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    if (g->ws_owned && g->ws) cudaFree(g->ws);
+    g->ws = dev_ptr;
+    g->ws_bytes = dev_ptr ? bytes : 0;
+    g->ws_owned = false;
+    return SW_OK;
+}
+
+static sw_status ensure_ws(sw_grid g, int prec, int k)
+{
+    size_t need = ws_layout(g, prec, k).total;
+    if (g->ws && g->ws_bytes >= need) return SW_OK;
+    if (g->ws && !g->ws_owned)
+        return fail(SW_ERR_INVALID_ARG, "attached workspace is smaller than sw_grid_workspace_bytes");
+    if (g->ws) { cudaFree(g->ws); g->ws = nullptr; g->ws_bytes = 0; }
+    CK(cudaMalloc(&g->ws, need));
+    g->ws_bytes = need;
+    g->ws_owned = true;
+    return SW_OK;
+}
+
+// ---------------------------------------------------------------------------
+// coefficients
+// ---------------------------------------------------------------------------
+static sw_status refactor(sw_grid g, cudaStream_t s)
+{
+    FactorArgs f;
+    f.nx = g->nx; f.ny = g->ny; f.eta_explicit = g->eta_explicit;
+    f.ax = g->ax; f.C = g->C; f.rowmax = g->rowmax;
+    f.lf = g->lf; f.invD = g->invD; f.zz = g->zz; f.gam = g->gam; f.ec = g->ec; f.eta_out = g->eta;
+    f.lf32 = g->lf32; f.invD32 = g->invD32; f.zz32 = g->zz32;
+    CK(launch_factor(f, row_threads(g->nx), s));
+    return SW_OK;
+}
+
+extern "C" sw_status sw_elliptic_set_coeffs(sw_grid g, const double *A11, const double *A12, const double *A21,
+                                            const double *A22, const double *B1, const double *B2, const double *C,
+                                            void *stream)
+{
+    if (!g) return fail(SW_ERR_INVALID_ARG, "sw_elliptic_set_coeffs: NULL grid");
+    if (!A11 || !A12 || !A21 || !A22 || !B1 || !B2 || !C)
+        return fail(SW_ERR_INVALID_ARG, "sw_elliptic_set_coeffs: NULL coefficient pointer");
+    cudaStream_t s = (cudaStream_t)stream;
+    FaceArgs a;
+    a.nx = g->nx; a.ny = g->ny; a.dlam = g->dlam; a.dphi = g->dphi;
+    a.A11 = A11; a.A12 = A12; a.A21 = A21; a.A22 = A22; a.B1 = B1; a.B2 = B2; a.C = C;
+    a.ax = g->ax; a.cx = g->cx; a.bx = g->bx; a.ay = g->ay; a.cy = g->cy; a.by = g->by; a.C64 = g->C; a.diag = g->diag;
+    a.wax = g->wax; a.wcx = g->wcx; a.wbx = g->wbx; a.way = g->way; a.wcy = g->wcy; a.wby = g->wby; a.wC = g->wC;
+    a.wdiag = g->wdiag; a.rowmax = g->rowmax;
+    CK(launch_faces(a, row_threads(g->nx), s));
+    sw_status st = refactor(g, s);
+    if (st) return st;
+    g->has_coeffs = true;
+    return SW_OK;
+}
+
+extern "C" sw_status sw_grid_set_eta(sw_grid g, double eta, void *stream)
+{
+    if (!g) return fail(SW_ERR_INVALID_ARG, "sw_grid_set_eta: NULL grid");
+    if (!std::isfinite(eta)) return fail(SW_ERR_INVALID_ARG, "sw_grid_set_eta: eta must be finite");
+    if (!g->has_coeffs) return fail(SW_ERR_INVALID_ARG, "sw_grid_set_eta: coefficients not set");
+    g->eta_explicit = eta > 0.0 ? eta : 0.0;
+    return refactor(g, (cudaStream_t)stream);
+}
+
+extern "C" sw_status sw_grid_get_eta(sw_grid g, double *eta)
+{
+    if (!g || !eta) return fail(SW_ERR_INVALID_ARG, "sw_grid_get_eta: NULL argument");
+    if (!g->has_coeffs) return fail(SW_ERR_INVALID_ARG, "sw_grid_get_eta: coefficients not set");
+    CK(cudaMemcpy(eta, g->eta, sizeof(double), cudaMemcpyDeviceToHost));
+    return SW_OK;
+}
+
+// ---------------------------------------------------------------------------
+// operator and preconditioner
+// ---------------------------------------------------------------------------
+extern "C" sw_status sw_operator_apply(sw_grid g, int prec, const void *x, void *y, void *stream)
+{
+    if (!g || !x || !y) return fail(SW_ERR_INVALID_ARG, "sw_operator_apply: NULL argument");
+    if (!g->has_coeffs) return fail(SW_ERR_INVALID_ARG, "sw_operator_apply: coefficients not set");
+    cudaStream_t s = (cudaStream_t)stream;
+    size_t eb = prec == SW_PREC_FP32 ? 4 : 8;
+    const char *xb = (const char *)x, *yb = (const char *)y;
+    if (xb < yb + g->N * eb && yb < xb + g->N * eb) return fail(SW_ERR_INVALID_ARG, "sw_operator_apply: x and y overlap");
+    if (prec == SW_PREC_FP64) {
+        OpArgs<double> a{g->nx, g->ny, g->ax, g->cx, g->bx, g->ay, g->cy, g->by, g->C};
+        CK(launch_operator_f64(a, (const double *)x, (double *)y, row_threads(g->nx), s));
+    } else if (prec == SW_PREC_FP32) {
+        OpArgs<float> a{g->nx, g->ny, g->wax, g->wcx, g->wbx, g->way, g->wcy, g->wby, g->wC};
+        CK(launch_operator_f32(a, (const float *)x, (float *)y, row_threads(g->nx), s));
+    } else {
+        return fail(SW_ERR_INVALID_ARG, "sw_operator_apply: prec must be SW_PREC_FP64 or SW_PREC_FP32");
+    }
+    return SW_OK;
+}
+
+static int pole_band(const sw_grid_s *g, const sw_solve_opts *o)
+{
+    if (o->prec == SW_PREC_FP64) return 0;
+    if (o->pole_band_rows >= 0) return std::min(o->pole_band_rows, g->ny / 2);
+    // 1 / 2 / 3 rows at ny = 64 / 128 / 256 (Sec. 4.3), one more per doubling
+    int l = 0;
+    while ((1 << (l + 1)) <= g->ny) ++l;
+    int b = l - 5;
+    if (b < 1) b = 1;
+    return std::min(b, g->ny / 2);
+}
+
+template <class Pol>
+static void fill_member(sw_grid g, const sw_solve_opts *o, const double *R, double *phi, MemberDev<Pol> &M)
+{
+    typedef typename Pol::coef ct;
+    typedef typename Pol::fac ft;
+    typedef typename Pol::vec vt;
+    typedef typename Pol::res rt;
+    typedef typename Pol::q16 qt;
+    std::memset(&M, 0, sizeof(M));
+    WsLayout L = ws_layout(g, o->prec, o->k);
+    char *w = (char *)g->ws;
+    M.nx = g->nx; M.ny = g->ny; M.k = o->k; M.pc = o->pc;
+    M.nstages = (o->pc == 2 || o->pc == 3) ? o->n_richardson : 1;
+    M.min_iters = o->min_iters; M.max_iters = o->max_iters; M.ru_every = o->ru_every;
+    M.band = pole_band(g, o);
+    M.tol = o->tol; M.omega = o->omega; M.etap = g->eta;
+    M.ax = g->ax; M.cx = g->cx; M.bx = g->bx; M.ay = g->ay; M.cy = g->cy; M.by = g->by; M.C = g->C;
+    if constexpr (Pol::kMixed) {
+        M.wax = (const ct *)g->wax; M.wcx = (const ct *)g->wcx; M.wbx = (const ct *)g->wbx;
+        M.way = (const ct *)g->way; M.wcy = (const ct *)g->wcy; M.wby = (const ct *)g->wby;
+        M.wC = (const ct *)g->wC; M.wdiag = (const ct *)g->wdiag;
+        M.lf = (const ft *)g->lf32; M.invD = (const ft *)g->invD32; M.zz = (const ft *)g->zz32;
+    } else {
+        M.wax = (const ct *)g->ax; M.wcx = (const ct *)g->cx; M.wbx = (const ct *)g->bx;
+        M.way = (const ct *)g->ay; M.wcy = (const ct *)g->cy; M.wby = (const ct *)g->by;
+        M.wC = (const ct *)g->C; M.wdiag = (const ct *)g->diag;
+        M.lf = (const ft *)g->lf; M.invD = (const ft *)g->invD; M.zz = (const ft *)g->zz;
+    }
+    M.gam = g->gam; M.ec = g->ec;
+    M.R = R; M.phi = phi;
+    M.r = (rt *)(w + L.r);
+    M.qa = (qt *)(w + L.qa); M.qb = (qt *)(w + L.qb); M.e = (qt *)(w + L.e);
+    if constexpr (Pol::kMixed) {
+        M.qa32 = (float *)(w + L.qa32); M.qb32 = (float *)(w + L.qb32); M.e32 = (float *)(w + L.e32);
+        M.qa_s = (float *)(w + L.qa_s); M.qb_s = (float *)(w + L.qb_s); M.e_s = (float *)(w + L.e_s);
+    }
+    M.Le = (vt *)(w + L.Le); M.p = (vt *)(w + L.p); M.Lp = (vt *)(w + L.Lp);
+    M.part = (double *)(w + L.part);
+    M.hist = o->res_history;
+    M.rowres = o->row_residual;
+}
+
+static sw_status upload_member(sw_grid g, const sw_solve_opts *o, const double *R, double *phi, cudaStream_t s,
+                               void *Mdev_out_host)
+{
+    if (o->prec == SW_PREC_FP64) {
+        MemberDev<PolFP64> M;
+        fill_member<PolFP64>(g, o, R, phi, M);
+        std::memcpy(Mdev_out_host, &M, sizeof(M));
+    } else if (o->prec == SW_PREC_MIXED_FP16) {
+        MemberDev<PolF16> M;
+        fill_member<PolF16>(g, o, R, phi, M);
+        std::memcpy(Mdev_out_host, &M, sizeof(M));
+    } else {
+        MemberDev<PolBF16> M;
+        fill_member<PolBF16>(g, o, R, phi, M);
+        std::memcpy(Mdev_out_host, &M, sizeof(M));
+    }
+    CK(cudaMemcpyAsync(g->blk->dev, Mdev_out_host, member_dev_bytes(o->prec), cudaMemcpyHostToDevice, s));
+    return SW_OK;
+}
+
+extern "C" sw_status sw_precond_apply(sw_grid g, const sw_solve_opts *o, const void *r, void *q, void *stream)
+{
+    if (!g || !r || !q) return fail(SW_ERR_INVALID_ARG, "sw_precond_apply: NULL argument");
+    if (!g->has_coeffs) return fail(SW_ERR_INVALID_ARG, "sw_precond_apply: coefficients not set");
+    sw_status st = check_opts(o, false);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    size_t eb = o->prec == SW_PREC_FP64 ? 8 : 4;
+    const char *rb = (const char *)r, *qb = (const char *)q;
+    if (rb < qb + g->N * eb && qb < rb + g->N * eb) return fail(SW_ERR_INVALID_ARG, "sw_precond_apply: r and q overlap");
+    if (o->eta > 0.0 && o->eta != g->eta_explicit) {
+        g->eta_explicit = o->eta;
+        if ((st = refactor(g, s))) return st;
+    }
+    if ((st = ensure_ws(g, o->prec, o->k))) return st;
+    alignas(16) unsigned char hbuf[sizeof(SolverBlock::dev)];
+    int nst = (o->pc == 2 || o->pc == 3) ? o->n_richardson : 1;
+    if (o->prec == SW_PREC_FP64) {
+        MemberDev<PolFP64> M;
+        fill_member<PolFP64>(g, o, nullptr, nullptr, M);
+        M.e = (double *)q;                    // FP64: the last stage writes q directly
+        std::memcpy(hbuf, &M, sizeof(M));
+    } else if (o->prec == SW_PREC_MIXED_FP16) {
+        MemberDev<PolF16> M;
+        fill_member<PolF16>(g, o, nullptr, nullptr, M);
+        std::memcpy(hbuf, &M, sizeof(M));
+    } else {
+        MemberDev<PolBF16> M;
+        fill_member<PolBF16>(g, o, nullptr, nullptr, M);
+        std::memcpy(hbuf, &M, sizeof(M));
+    }
+    CK(cudaMemcpyAsync(g->blk->dev, hbuf, member_dev_bytes(o->prec), cudaMemcpyHostToDevice, s));
+    CK(launch_precond(o->prec, g->blk->dev, g->nx, g->ny, nst, r, o->prec == SW_PREC_FP64 ? nullptr : q,
+                      row_threads(g->nx), s));
+    // the host staging buffer must outlive the asynchronous copy
+    CK(cudaStreamSynchronize(s));
+    return SW_OK;
+}
+
+// ---------------------------------------------------------------------------
+// solves
+// ---------------------------------------------------------------------------
+static sw_status solve_members(int n, const sw_grid *grids, const sw_solve_opts *o, const double *const *R,
+                               double *const *phi, sw_solve_stats *stats, cudaStream_t s)
+{
+    sw_status st = check_opts(o, true);
+    if (st) return st;
+    if (n < 1 || n > MAX_MEMBERS) return fail(SW_ERR_INVALID_ARG, "number of members must be 1..480");
+    int dev = -1;
+    CK(cudaGetDevice(&dev));
+    int max_nx = 0, total_rows = 0;
+    for (int m = 0; m < n; ++m) {
+        sw_grid g = grids[m];
+        if (!g) return fail(SW_ERR_INVALID_ARG, "NULL grid in the member list");
+        if (!R[m] || !phi[m]) return fail(SW_ERR_INVALID_ARG, "NULL R or phi");
+        if (!g->has_coeffs) return fail(SW_ERR_INVALID_ARG, "coefficients not set for a member grid");
+        if (g->device != dev) return fail(SW_ERR_INVALID_ARG, "member grid belongs to another device");
+        for (int q = 0; q < m; ++q)
+            if (grids[q] == g) return fail(SW_ERR_INVALID_ARG, "the member grids must be distinct");
+        if (n > 1 && (o->res_history || o->row_residual))
+            return fail(SW_ERR_INVALID_ARG, "res_history / row_residual are for single solves");
+        max_nx = std::max(max_nx, g->nx);
+        total_rows += g->ny;
+    }
+    EnsembleParams P;
+    P.n = n;
+    static thread_local std::vector<unsigned char> staging;
+    staging.resize((size_t)n * sizeof(SolverBlock::dev));
+    for (int m = 0; m < n; ++m) {
+        sw_grid g = grids[m];
+        if (o->eta > 0.0 && o->eta != g->eta_explicit) {
+            g->eta_explicit = o->eta;
+            if ((st = refactor(g, s))) return st;
+        }
+        if ((st = ensure_ws(g, o->prec, o->k))) return st;
+        if ((st = upload_member(g, o, R[m], phi[m], s, staging.data() + (size_t)m * sizeof(SolverBlock::dev)))) return st;
+        MemberCtl c;
+        std::memset(&c, 0, sizeof(c));
+        c.phase = PH_TRUE;
+        c.init = 1;
+        *g->h_ctl = c;
+        CK(cudaMemcpyAsync(&g->blk->ctl, g->h_ctl, sizeof(MemberCtl), cudaMemcpyHostToDevice, s));
+        CK(cudaMemsetAsync(&g->blk->g, 0, sizeof(GlobalCtl), s));
+        P.blk[m] = g->blk;
+    }
+    if (o->res_history) CK(launch_fill(o->res_history, (size_t)o->max_iters + 1, NAN, s));
+    int threads = row_threads(max_nx);
+    int grid_used = 0;
+    CK(launch_gcr(o->prec, P, max_nx, threads, grids[0]->sms, total_rows, s, &grid_used));
+    for (int m = 0; m < n; ++m) {
+        sw_grid g = grids[m];
+        CK(cudaMemcpyAsync(g->h_ctl, &g->blk->ctl, sizeof(MemberCtl) + sizeof(GlobalCtl), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(g->h_eta, g->eta, sizeof(double), cudaMemcpyDeviceToHost, s));
+    }
+    CK(cudaStreamSynchronize(s));
+    sw_status first = SW_OK;
+    bool timeout = grids[0]->h_g->abort != 0;
+    for (int m = 0; m < n; ++m) {
+        sw_grid g = grids[m];
+        const MemberCtl &c = *g->h_ctl;
+        int mst = timeout ? SW_ERR_TIMEOUT : (c.phase == PH_DONE ? c.status : SW_ERR_INTERNAL);
+        if (stats) {
+            sw_solve_stats &S = stats[m];
+            std::memset(&S, 0, sizeof(S));
+            S.iterations = c.it;
+            S.status = mst;
+            S.converged = (mst == SW_OK);
+            S.r0_norm = c.r0;
+            S.R_norm = c.nR;
+            S.true_rel_residual = c.nR > 0 ? c.rn_true / c.nR : 0.0;
+            S.recursive_rel_residual = c.nR > 0 ? c.rn_rec / c.nR : 0.0;
+            S.eta = *g->h_eta;
+        }
+        if (mst != SW_OK && first == SW_OK) first = (sw_status)mst;
+    }
+    if (timeout) return fail(SW_ERR_TIMEOUT, "a device-side barrier wait ran out");
+    if (first == SW_ERR_NOT_CONVERGED) g_err = "max_iters reached before the tolerance";
+    else if (first == SW_ERR_BREAKDOWN) g_err = "GCR breakdown: <L p, L p> not positive";
+    else if (first == SW_ERR_NONFINITE) g_err = "non-finite residual norm";
+    else if (first == SW_ERR_INTERNAL) g_err = "solver ended in an unexpected state";
+    return first;
+}
+
+extern "C" sw_status sw_gcr_solve(sw_grid g, const sw_solve_opts *o, const double *R, double *phi,
+                                  sw_solve_stats *stats, void *stream)
+{
+    if (!g || !R || !phi) return fail(SW_ERR_INVALID_ARG, "sw_gcr_solve: NULL argument");
+    const double *Rs[1] = {R};
+    double *Ps[1] = {phi};
+    return solve_members(1, &g, o, Rs, Ps, stats, (cudaStream_t)stream);
+}
+
+extern "C" sw_status sw_ensemble_solve(int n, const sw_grid *grids, const sw_solve_opts *o, const double *const *R,
+                                       double *const *phi, sw_solve_stats *stats, void *stream)
+{
+    if (!grids || !R || !phi) return fail(SW_ERR_INVALID_ARG, "sw_ensemble_solve: NULL argument");
+    return solve_members(n, grids, o, R, phi, stats, (cudaStream_t)stream);
+}

@@ -1,0 +1,217 @@
+// sw_setup.cu -- work done once per set of coefficients (sw_elliptic_set_coeffs):
+//  * face coefficients of the flux-form operator (Eq. 10) in FP64 and FP32,
+//    the diagonal of L (preconditioner options 1 and 2) and, per row, the
+//    largest |diag(P^M)| (for the automatic pseudo time step of Eq. 13);
+//  * the factorised zonal operator T = I - eta (P^Z - P^H) of every row: a
+//    symmetric cyclic tridiagonal matrix, split by Sherman-Morrison into its
+//    plain tridiagonal part T' = L D L^T and a rank-one wrap correction.
+// The pivots D_i follow the continued fraction D_i = d_i - o_{i-1}^2 / D_{i-1};
+// written as the three-term recurrence of the leading minors it is a product
+// of 2x2 transfer matrices, which a block computes with a parallel scan.
+#include "sw_common.cuh"
+#include "sw_internal.h"
+
+namespace sw {
+
+__global__ void __launch_bounds__(MAX_THREADS) k_faces(FaceArgs a)
+{
+    __shared__ double red[MAX_THREADS / 32];
+    const int nx = a.nx, ny = a.ny, j = blockIdx.x;
+    const double idl2 = 1.0 / (a.dlam * a.dlam), idp2 = 1.0 / (a.dphi * a.dphi);
+    const double i4 = 1.0 / (4.0 * a.dlam * a.dphi), i2l = 1.0 / (2.0 * a.dlam), i2p = 1.0 / (2.0 * a.dphi);
+    const size_t row = (size_t)j * nx;
+    double m = 0.0;
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+        const int ip = (i + 1 == nx) ? 0 : i + 1, im = (i == 0) ? nx - 1 : i - 1;
+        const size_t id = row + i;
+        // x faces i+1/2 and i-1/2 of row j
+        double ax = 0.5 * (a.A11[id] + a.A11[row + ip]) * idl2;
+        double cx = 0.5 * (a.A12[id] + a.A12[row + ip]) * i4;
+        double bx = 0.5 * (a.B1[id] + a.B1[row + ip]) * i2l;
+        double axm = 0.5 * (a.A11[row + im] + a.A11[id]) * idl2;
+        double bxm = 0.5 * (a.B1[row + im] + a.B1[id]) * i2l;
+        // y faces j+1/2 and j-1/2 (zero through the pole faces)
+        double ay = 0.0, cy = 0.0, by = 0.0, ays = 0.0, bys = 0.0;
+        if (j < ny - 1) {
+            ay = 0.5 * (a.A22[id] + a.A22[id + nx]) * idp2;
+            cy = 0.5 * (a.A21[id] + a.A21[id + nx]) * i4;
+            by = 0.5 * (a.B2[id] + a.B2[id + nx]) * i2p;
+        }
+        if (j > 0) {
+            ays = 0.5 * (a.A22[id - nx] + a.A22[id]) * idp2;
+            bys = 0.5 * (a.B2[id - nx] + a.B2[id]) * i2p;
+        }
+        const double c = a.C[id];
+        // diagonal of P^M = L - P^Z + P^H, and of L
+        const double dpm = (bx - bxm) - (ay + ays) + (by - bys);
+        const double dl = -(ax + axm) + dpm - c;
+        a.ax[id] = ax; a.cx[id] = cx; a.bx[id] = bx;
+        a.ay[id] = ay; a.cy[id] = cy; a.by[id] = by;
+        a.C64[id] = c; a.diag[id] = dl;
+        a.wax[id] = (float)ax; a.wcx[id] = (float)cx; a.wbx[id] = (float)bx;
+        a.way[id] = (float)ay; a.wcy[id] = (float)cy; a.wby[id] = (float)by;
+        a.wC[id] = (float)c; a.wdiag[id] = (float)dl;
+        m = fmax(m, fabs(dpm));
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) red[w] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double mm = 0.0;
+        for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) mm = fmax(mm, red[ww]);
+        a.rowmax[j] = mm;
+    }
+}
+
+// 2x2 matrix [[m00, m01], [m10, m11]]
+struct M2 { double m00, m01, m10, m11; };
+
+__device__ __forceinline__ M2 mul(const M2 &A, const M2 &B)   // A B
+{
+    return {A.m00 * B.m00 + A.m01 * B.m10, A.m00 * B.m01 + A.m01 * B.m11,
+            A.m10 * B.m00 + A.m11 * B.m10, A.m10 * B.m01 + A.m11 * B.m11};
+}
+
+// scale by a power of two so that the largest entry is O(1) (ratios unchanged)
+__device__ __forceinline__ void renorm(M2 &A)
+{
+    double m = fmax(fmax(fabs(A.m00), fabs(A.m01)), fmax(fabs(A.m10), fabs(A.m11)));
+    if (m > 0.0 && isfinite(m)) {
+        int e;
+        frexp(m, &e);
+        A.m00 = ldexp(A.m00, -e); A.m01 = ldexp(A.m01, -e);
+        A.m10 = ldexp(A.m10, -e); A.m11 = ldexp(A.m11, -e);
+    }
+}
+
+__device__ __forceinline__ M2 shfl_up(const M2 &A, int d)
+{
+    return {__shfl_up_sync(0xffffffffu, A.m00, d), __shfl_up_sync(0xffffffffu, A.m01, d),
+            __shfl_up_sync(0xffffffffu, A.m10, d), __shfl_up_sync(0xffffffffu, A.m11, d)};
+}
+
+// exclusive block scan of matrices in thread order: returns the product of
+// the matrices of all earlier threads (later ones on the left)
+__device__ M2 scan_mat_excl(M2 A, M2 *sm)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    M2 inc = A;
+    for (int d = 1; d < 32; d <<= 1) {
+        M2 o = shfl_up(inc, d);
+        if (lane >= d) { inc = mul(inc, o); renorm(inc); }
+    }
+    M2 ex = shfl_up(inc, 1);
+    if (lane == 0) ex = {1.0, 0.0, 0.0, 1.0};
+    if (lane == 31) sm[w] = inc;
+    __syncthreads();
+    M2 pre = {1.0, 0.0, 0.0, 1.0};
+    for (int ww = 0; ww < w; ++ww) { pre = mul(sm[ww], pre); renorm(pre); }
+    M2 out = mul(ex, pre);
+    renorm(out);
+    __syncthreads();
+    return out;
+}
+
+__global__ void __launch_bounds__(MAX_THREADS) k_factor(FactorArgs a)
+{
+    extern __shared__ __align__(16) unsigned char dsm[];
+    double *sb = (double *)dsm;                          // nx
+    __shared__ M2 smat[MAX_THREADS / 32];
+    __shared__ double sscan[2 * (MAX_THREADS / 32)];
+    __shared__ double red[MAX_THREADS / 32];
+    __shared__ double s_eta;
+    const int nx = a.nx, ny = a.ny, j = blockIdx.x;
+    const size_t row = (size_t)j * nx;
+
+    // eta: explicit, or 1 / max |diag(P^M)| over the grid
+    if (a.eta_explicit > 0.0) {
+        if (threadIdx.x == 0) s_eta = a.eta_explicit;
+    } else {
+        double m = 0.0;
+        for (int r = threadIdx.x; r < ny; r += blockDim.x) m = fmax(m, a.rowmax[r]);
+        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double mm = 0.0;
+            for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) mm = fmax(mm, red[ww]);
+            s_eta = mm > 0.0 ? 1.0 / mm : 1.0;
+        }
+    }
+    __syncthreads();
+    const double eta = s_eta;
+    if (j == 0 && threadIdx.x == 0) *a.eta_out = eta;
+
+    // row of T: diag_i = 1 + eta (ax_i + ax_{i-1} + C_i); coupling of i and
+    // i+1: o_i = -eta ax_i (o_{nx-1} couples the last point to the first)
+    const double *ax = a.ax + row, *C = a.C + row;
+    auto diagT = [&](int i) { int im = (i == 0) ? nx - 1 : i - 1; return 1.0 + eta * (ax[i] + ax[im] + C[i]); };
+    const double ec = -eta * ax[nx - 1];
+    const double d0 = diagT(0);
+    const double gam = -d0;
+    // T' = T minus the rank-one wrap term w w^T / gam, w = (gam, 0, .., 0, ec)
+    auto dprime = [&](int i) {
+        double d = diagT(i);
+        if (i == 0) d -= gam;
+        if (i == nx - 1) d -= ec * ec / gam;
+        return d;
+    };
+    int c0, c1;
+    row_chunk(nx, c0, c1);
+    // product of the transfer matrices [[d'_i, -o_{i-1}^2], [1, 0]] of my chunk
+    M2 P = {1.0, 0.0, 0.0, 1.0};
+    for (int i = c0; i < c1; ++i) {
+        double o = (i == 0) ? 0.0 : -eta * ax[i - 1];
+        M2 Mi = {dprime(i), -o * o, 1.0, 0.0};
+        P = mul(Mi, P);
+        renorm(P);
+    }
+    M2 Q = scan_mat_excl(P, smat);
+    // pivot before my chunk: D_{c0-1} = theta_{c0-1} / theta_{c0-2} = Q00 / Q10
+    double Dprev = (c0 > 0) ? Q.m00 / Q.m10 : 0.0;
+    for (int i = c0; i < c1; ++i) {
+        double l = 0.0, D;
+        if (i == 0) {
+            D = dprime(0);
+        } else {
+            double o = -eta * ax[i - 1];
+            l = o / Dprev;
+            D = dprime(i) - l * o;
+        }
+        a.lf[row + i] = l;
+        a.invD[row + i] = 1.0 / D;
+        Dprev = D;
+    }
+    __syncthreads();
+    // z = T'^{-1} w
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) sb[i] = (i == 0) ? gam : ((i == nx - 1) ? ec : 0.0);
+    __syncthreads();
+    trisolve_row<double, double>(sb, nx, a.lf + row, a.invD + row, (const double *)nullptr, 0.0, 0.0, sscan);
+    const double g = 1.0 / (gam + gam * sb[0] + ec * sb[nx - 1]);
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+        double z = sb[i] * g;
+        a.zz[row + i] = z;
+        a.zz32[row + i] = (float)z;
+        a.lf32[row + i] = (float)a.lf[row + i];
+        a.invD32[row + i] = (float)a.invD[row + i];
+    }
+    if (threadIdx.x == 0) { a.gam[j] = gam; a.ec[j] = ec; }
+}
+
+cudaError_t launch_faces(const FaceArgs &a, int threads, cudaStream_t s)
+{
+    k_faces<<<a.ny, threads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_factor(const FactorArgs &a, int threads, cudaStream_t s)
+{
+    size_t smem = (size_t)a.nx * sizeof(double);
+    cudaError_t e = cudaFuncSetAttribute(k_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_factor<<<a.ny, threads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+} // namespace sw

@@ -68,8 +68,19 @@ def sh_modes(lmin: int, lmax: int):
 
 
 def random_sh_field(lam, phi, coeffs: np.ndarray, modes) -> np.ndarray:
-    """Sum_k coeffs[k] * Y_{modes[k]} on the grid."""
-    out = np.zeros((phi.size, lam.size))
+    """Sum_k coeffs[k] * Y_{modes[k]} on the grid, evaluated separably: the
+    latitude factors are summed per zonal wavenumber first, then one small
+    matrix product with the longitude factors gives the field."""
+    mmax = max(abs(m) for _, m in modes)
+    lat = np.zeros((phi.size, 2 * mmax + 1))
     for c, (l, m) in zip(coeffs, modes):
-        out += c * real_sh(l, m, lam, phi)
-    return out
+        am = abs(m)
+        norm = math.sqrt((2 * l + 1) / (4.0 * math.pi)
+                         * math.factorial(l - am) / math.factorial(l + am))
+        if m != 0:
+            norm *= math.sqrt(2.0)
+        lat[:, m + mmax] += c * norm * _assoc_legendre(l, am, np.sin(phi))
+    lon = np.empty((2 * mmax + 1, lam.size))
+    for m in range(-mmax, mmax + 1):
+        lon[m + mmax] = np.cos(m * lam) if m > 0 else (np.sin(-m * lam) if m < 0 else 1.0)
+    return lat @ lon
