@@ -72,7 +72,7 @@ typedef enum {
 } sw_precond_kind;
 
 typedef struct {
-    int k;               /* GCR(k): directions kept before a restart (1..16) */
+    int k;               /* GCR(k): directions kept before a restart (1..8) */
     double tol;          /* exit when ||L(Phi) - R||_2 <= tol ||R||_2 (Eq. 12 with
                             ||R|| in place of ||r_0||; equal for a zero first guess) */
     int max_iters;       /* >= 1 */
@@ -88,6 +88,8 @@ typedef struct {
                             preconditioner runs in FP32 (Sec. 4.3); -1: automatic */
     int ru_every;        /* recompute the true residual every ru_every
                             iterations (0: only when the exit test is met) */
+    int threads_per_row; /* launch shape: threads of the block that works on one
+                            latitude row (multiple of 32, <= 256); 0: automatic */
     double *res_history; /* device, optional (NULL): max_iters+1 doubles, the
                             relative residual after each iteration (entry 0:
                             the initial one), NaN where not reached */
@@ -159,7 +161,7 @@ sw_status sw_precond_apply(sw_grid g, const sw_solve_opts *o, const void *r, voi
 sw_status sw_gcr_solve(sw_grid g, const sw_solve_opts *o, const double *R, double *phi,
                        sw_solve_stats *stats, void *stream);
 
-/* Solve n independent problems (grids may differ in size) in one persistent
+/* Solve n (1..480) independent problems (grids may differ in size) in one persistent
  * launch; each member stops at its own convergence.  grids, R, phi and stats
  * are host arrays of n entries (R[m], phi[m] device pointers).  The grids must
  * be distinct.  Returns the first non-OK member status, else SW_OK. */

@@ -31,6 +31,7 @@ class SolveOpts(C.Structure):
     _fields_ = [("k", C.c_int), ("tol", C.c_double), ("max_iters", C.c_int), ("min_iters", C.c_int),
                 ("pc", C.c_int), ("n_richardson", C.c_int), ("eta", C.c_double), ("omega", C.c_double),
                 ("prec", C.c_int), ("pole_band_rows", C.c_int), ("ru_every", C.c_int),
+                ("threads_per_row", C.c_int),
                 ("res_history", C.c_void_p), ("row_residual", C.c_void_p)]
 
 

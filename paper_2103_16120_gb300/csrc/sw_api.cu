@@ -47,15 +47,21 @@ struct sw_grid_s {
     size_t ws_bytes;
     bool ws_owned;
     SolverBlock *blk;              // device: member state of this grid
+    EnsDesc *desc;                 // device: launch descriptor when this grid leads a launch
+    EnsDesc *h_desc;               // pinned host staging of desc
     MemberCtl *h_ctl;              // pinned host copies read after a solve
     GlobalCtl *h_g;
     double *h_eta;
 };
 
-static int row_threads(int nx)
+// threads of the block that works on one row: about four values per thread,
+// at least nx/16 (the tridiagonal chunks live in registers, 16 values at most)
+static int row_threads(int nx, int requested = 0)
 {
-    int t = ((nx / 4 + 31) / 32) * 32;
-    if (t < 64) t = 64;
+    int t = requested > 0 ? requested : ((nx / 4 + 31) / 32) * 32;
+    const int tmin = ((nx + 16 * 32 - 1) / (16 * 32)) * 32;
+    if (t < tmin) t = tmin;
+    if (t < 32) t = 32;
     if (t > MAX_THREADS) t = MAX_THREADS;
     return t;
 }
@@ -99,10 +105,14 @@ extern "C" sw_status sw_grid_create(int nx, int ny, double radius, sw_grid *out)
     size_t bytes = 11 * al(N * 8) + 3 * al((size_t)ny * 8) + al(8) + 11 * al(N * 4);
     if (e == cudaSuccess) e = cudaMalloc(&g->cmem, bytes);
     if (e == cudaSuccess) e = cudaMalloc((void **)&g->blk, sizeof(SolverBlock));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&g->desc, sizeof(EnsDesc));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&g->h_desc, sizeof(EnsDesc));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&g->h_ctl, sizeof(MemberCtl) + sizeof(GlobalCtl) + 64);
     if (e != cudaSuccess) {
         if (g->cmem) cudaFree(g->cmem);
         if (g->blk) cudaFree(g->blk);
+        if (g->desc) cudaFree(g->desc);
+        if (g->h_desc) cudaFreeHost(g->h_desc);
         delete g;
         return cuda_fail(e, "sw_grid_create");
     }
@@ -126,6 +136,8 @@ extern "C" sw_status sw_grid_destroy(sw_grid g)
     if (!g) return fail(SW_ERR_INVALID_ARG, "sw_grid_destroy: NULL grid");
     cudaFree(g->cmem);
     cudaFree(g->blk);
+    cudaFree(g->desc);
+    cudaFreeHost(g->h_desc);
     if (g->ws_owned && g->ws) cudaFree(g->ws);
     cudaFreeHost(g->h_ctl);
     delete g;
@@ -155,7 +167,7 @@ static WsLayout ws_layout(const sw_grid_s *g, int prec, int k)
     L.Le = take(N * v);
     L.p = take(N * v * (k + 1));
     L.Lp = take(N * v * (k + 1));
-    L.part = take(ny * NSLOT * 8);
+    L.part = take(2 * ny * NSLOT * 8);
     L.total = off;
     return L;
 }
@@ -163,7 +175,7 @@ static WsLayout ws_layout(const sw_grid_s *g, int prec, int k)
 static sw_status check_opts(const sw_solve_opts *o, bool solve)
 {
     if (!o) return fail(SW_ERR_INVALID_ARG, "options are NULL");
-    if (o->k < 1 || o->k > KMAX) return fail(SW_ERR_INVALID_ARG, "k must be 1..16");
+    if (o->k < 1 || o->k > KMAX) return fail(SW_ERR_INVALID_ARG, "k must be 1..8");
     if (o->pc < 0 || o->pc > 3) return fail(SW_ERR_INVALID_ARG, "pc must be 0..3");
     if ((o->pc == 2 || o->pc == 3) && (o->n_richardson < 1 || o->n_richardson > 16))
         return fail(SW_ERR_INVALID_ARG, "n_richardson must be 1..16");
@@ -174,6 +186,8 @@ static sw_status check_opts(const sw_solve_opts *o, bool solve)
         if (o->ru_every < 0) return fail(SW_ERR_INVALID_ARG, "ru_every must be >= 0");
     }
     if (o->pc == 2 && !(std::isfinite(o->omega))) return fail(SW_ERR_INVALID_ARG, "omega must be finite");
+    if (o->threads_per_row < 0 || o->threads_per_row > MAX_THREADS || (o->threads_per_row & 31))
+        return fail(SW_ERR_INVALID_ARG, "threads_per_row must be 0 or a multiple of 32 up to 256");
     if (!std::isfinite(o->eta)) return fail(SW_ERR_INVALID_ARG, "eta must be finite");
     return SW_OK;
 }
@@ -382,20 +396,23 @@ extern "C" sw_status sw_precond_apply(sw_grid g, const sw_solve_opts *o, const v
     if (o->prec == SW_PREC_FP64) {
         MemberDev<PolFP64> M;
         fill_member<PolFP64>(g, o, nullptr, nullptr, M);
+        M.r = (double *)r;                    // the stages read r from the member's r
         M.e = (double *)q;                    // FP64: the last stage writes q directly
         std::memcpy(hbuf, &M, sizeof(M));
     } else if (o->prec == SW_PREC_MIXED_FP16) {
         MemberDev<PolF16> M;
         fill_member<PolF16>(g, o, nullptr, nullptr, M);
+        M.r = (float *)r;
         std::memcpy(hbuf, &M, sizeof(M));
     } else {
         MemberDev<PolBF16> M;
         fill_member<PolBF16>(g, o, nullptr, nullptr, M);
+        M.r = (float *)r;
         std::memcpy(hbuf, &M, sizeof(M));
     }
     CK(cudaMemcpyAsync(g->blk->dev, hbuf, member_dev_bytes(o->prec), cudaMemcpyHostToDevice, s));
-    CK(launch_precond(o->prec, g->blk->dev, g->nx, g->ny, nst, r, o->prec == SW_PREC_FP64 ? nullptr : q,
-                      row_threads(g->nx), s));
+    CK(launch_precond(o->prec, g->blk->dev, g->nx, g->ny, nst, o->prec == SW_PREC_FP64 ? nullptr : q,
+                      row_threads(g->nx, o->threads_per_row), s));
     // the host staging buffer must outlive the asynchronous copy
     CK(cudaStreamSynchronize(s));
     return SW_OK;
@@ -412,7 +429,7 @@ static sw_status solve_members(int n, const sw_grid *grids, const sw_solve_opts 
     if (n < 1 || n > MAX_MEMBERS) return fail(SW_ERR_INVALID_ARG, "number of members must be 1..480");
     int dev = -1;
     CK(cudaGetDevice(&dev));
-    int max_nx = 0, total_rows = 0;
+    int max_nx = 0;
     for (int m = 0; m < n; ++m) {
         sw_grid g = grids[m];
         if (!g) return fail(SW_ERR_INVALID_ARG, "NULL grid in the member list");
@@ -424,10 +441,7 @@ static sw_status solve_members(int n, const sw_grid *grids, const sw_solve_opts 
         if (n > 1 && (o->res_history || o->row_residual))
             return fail(SW_ERR_INVALID_ARG, "res_history / row_residual are for single solves");
         max_nx = std::max(max_nx, g->nx);
-        total_rows += g->ny;
     }
-    EnsembleParams P;
-    P.n = n;
     static thread_local std::vector<unsigned char> staging;
     staging.resize((size_t)n * sizeof(SolverBlock::dev));
     for (int m = 0; m < n; ++m) {
@@ -442,15 +456,70 @@ static sw_status solve_members(int n, const sw_grid *grids, const sw_solve_opts 
         std::memset(&c, 0, sizeof(c));
         c.phase = PH_TRUE;
         c.init = 1;
+        c.nu = -1;
         *g->h_ctl = c;
         CK(cudaMemcpyAsync(&g->blk->ctl, g->h_ctl, sizeof(MemberCtl), cudaMemcpyHostToDevice, s));
         CK(cudaMemsetAsync(&g->blk->g, 0, sizeof(GlobalCtl), s));
-        P.blk[m] = g->blk;
     }
     if (o->res_history) CK(launch_fill(o->res_history, (size_t)o->max_iters + 1, NAN, s));
-    int threads = row_threads(max_nx);
-    int grid_used = 0;
-    CK(launch_gcr(o->prec, P, max_nx, threads, grids[0]->sms, total_rows, s, &grid_used));
+
+    // Launch shape: every member owns a group of blocks and every block one
+    // latitude row when the co-resident blocks suffice, so the row's constant
+    // data and owner-only vectors stay in shared memory; otherwise the blocks
+    // cycle over several rows with everything in global memory.
+    const int sms = grids[0]->sms;
+    const int threads = row_threads(max_nx, o->threads_per_row);
+    std::vector<int> nb(n, 1);
+    int grid = 0, cc = 0, cs = 0;
+    size_t smem = 0;
+    const int levels[3][2] = {{1, 1}, {1, 0}, {0, 0}};
+    long rows_total = 0;
+    for (int m = 0; m < n; ++m) rows_total += grids[m]->ny;
+    for (int lv = 0; lv < 3 && !grid; ++lv) {
+        const size_t sm_l = gcr_smem_bytes(o->prec, max_nx, o->k, levels[lv][0], levels[lv][1]);
+        int bps = 0;
+        CK(gcr_occupancy(o->prec, threads, sm_l, &bps));
+        if (bps > 0 && rows_total <= (long)bps * sms) {
+            for (int m = 0; m < n; ++m) nb[m] = grids[m]->ny;
+            grid = (int)rows_total; cc = levels[lv][0]; cs = levels[lv][1]; smem = sm_l;
+        }
+    }
+    if (!grid) {
+        // several rows per block: spread the co-resident blocks over the members
+        smem = gcr_smem_bytes(o->prec, max_nx, o->k, 0, 0);
+        int bps = 0;
+        CK(gcr_occupancy(o->prec, threads, smem, &bps));
+        if (bps < 1) return fail(SW_ERR_INVALID_ARG, "grid rows too long for the solver kernel");
+        const int cap = bps * sms;
+        if (n > cap) return fail(SW_ERR_INVALID_ARG, "too many members for one launch on this device");
+        int used = n;
+        while (used < cap) {
+            int best = -1;
+            double bw = 0.0;
+            for (int m = 0; m < n; ++m) {
+                if (nb[m] >= grids[m]->ny) continue;
+                double wgt = (double)grids[m]->ny * grids[m]->nx / nb[m];
+                if (wgt > bw) { bw = wgt; best = m; }
+            }
+            if (best < 0) break;
+            ++nb[best];
+            ++used;
+        }
+        grid = used;
+    }
+    sw_grid lead = grids[0];
+    EnsDesc &D = *lead->h_desc;
+    D.n = n;
+    D.grid = grid;
+    D.cache_const = cc;
+    D.cache_state = cs;
+    D.cta_begin[0] = 0;
+    for (int m = 0; m < n; ++m) {
+        D.cta_begin[m + 1] = D.cta_begin[m] + nb[m];
+        D.blk[m] = grids[m]->blk;
+    }
+    CK(cudaMemcpyAsync(lead->desc, &D, sizeof(EnsDesc), cudaMemcpyHostToDevice, s));
+    CK(launch_gcr(o->prec, lead->desc, grid, max_nx, threads, smem, s));
     for (int m = 0; m < n; ++m) {
         sw_grid g = grids[m];
         CK(cudaMemcpyAsync(g->h_ctl, &g->blk->ctl, sizeof(MemberCtl) + sizeof(GlobalCtl), cudaMemcpyDeviceToHost, s));
@@ -458,10 +527,12 @@ static sw_status solve_members(int n, const sw_grid *grids, const sw_solve_opts 
     }
     CK(cudaStreamSynchronize(s));
     sw_status first = SW_OK;
-    bool timeout = grids[0]->h_g->abort != 0;
+    bool any_timeout = false;
     for (int m = 0; m < n; ++m) {
         sw_grid g = grids[m];
         const MemberCtl &c = *g->h_ctl;
+        const bool timeout = g->h_g->abort != 0;
+        any_timeout |= timeout;
         int mst = timeout ? SW_ERR_TIMEOUT : (c.phase == PH_DONE ? c.status : SW_ERR_INTERNAL);
         if (stats) {
             sw_solve_stats &S = stats[m];
@@ -477,7 +548,7 @@ static sw_status solve_members(int n, const sw_grid *grids, const sw_solve_opts 
         }
         if (mst != SW_OK && first == SW_OK) first = (sw_status)mst;
     }
-    if (timeout) return fail(SW_ERR_TIMEOUT, "a device-side barrier wait ran out");
+    if (any_timeout) return fail(SW_ERR_TIMEOUT, "a device-side barrier wait ran out");
     if (first == SW_ERR_NOT_CONVERGED) g_err = "max_iters reached before the tolerance";
     else if (first == SW_ERR_BREAKDOWN) g_err = "GCR breakdown: <L p, L p> not positive";
     else if (first == SW_ERR_NONFINITE) g_err = "non-finite residual norm";

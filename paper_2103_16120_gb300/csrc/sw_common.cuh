@@ -10,19 +10,19 @@
 
 namespace sw {
 
-constexpr int KMAX = 16;            // largest GCR k
-constexpr int NSLOT = 4 + KMAX;     // partial sums kept per row
-constexpr int S_RR = 0;             // ||r||^2
-constexpr int S_R2 = 1;             // ||R||^2 (first phase only)
-constexpr int S_LPLP = 2;           // <L p_new, L p_new>
-constexpr int S_RLP = 3;            // <r, L p_new>
-constexpr int S_DOT0 = 4;           // <L e, L p_l>, l = 0..nu
-constexpr int MAX_MEMBERS = 480;    // members of one ensemble launch (kernel parameters < 4 KB)
+constexpr int KMAX = 8;             // largest GCR k
+// row partial sums kept per row and phase (two buffers by phase parity):
+//   PH_TRUE: ||r||^2, ||R||^2
+//   PH_LE:   <Le,Le>, <r,Le>, <Le,Lp_l> (l < nd), <r,Lp_l> (l < nd)
+//   PH_UB:   ||r||^2, <Lp_new,Lp_new>, <Lp_new,Lp_m> (m < nd)
+constexpr int NSLOT = 2 + 2 * KMAX;
+constexpr int S_A = 0, S_B = 1, S_C0 = 2, S_T0 = 2 + KMAX;
+constexpr int MAX_MEMBERS = 480;    // members of one ensemble launch
 constexpr int MAX_NX = 4096;
 constexpr int MAX_THREADS = 256;    // block size of the row kernels
 
 // phase kinds of the GCR state machine (see sw_solver.cu)
-enum Phase : int { PH_TRUE = 0, PH_BETA = 1, PH_PREC = 2, PH_LE = 3, PH_UPD = 4, PH_ZERO = 5, PH_DONE = 6 };
+enum Phase : int { PH_TRUE = 0, PH_UB = 1, PH_PREC = 2, PH_LE = 3, PH_ZERO = 5, PH_DONE = 6 };
 
 // status codes (mirror sw_status)
 enum : int { ST_OK = 0, ST_INVALID = 1, ST_CUDA = 2, ST_OOM = 3, ST_NOT_CONVERGED = 4,
@@ -54,6 +54,12 @@ struct PolBF16 {
     typedef float vec;  typedef float res;  typedef __nv_bfloat16 q16;
     static constexpr bool kMixed = true;
 };
+
+// accumulation type of the inner products within a warp: FP64 for the FP64
+// policy; FP32 for the mixed policies (block and member sums are FP64)
+template <class Pol> struct Acc { typedef double type; };
+template <> struct Acc<PolF16> { typedef float type; };
+template <> struct Acc<PolBF16> { typedef float type; };
 
 __device__ __forceinline__ float q_to_f(__half h) { return __half2float(h); }
 __device__ __forceinline__ float q_to_f(__nv_bfloat16 h) { return __bfloat162float(h); }
@@ -98,24 +104,23 @@ struct MemberDev {
     float *qa32, *qb32, *e32;       // FP32 storage of the pole-band rows (mixed)
     float *qa_s, *qb_s, *e_s;       // per-row scales of the 16-bit storage
     vec_t *Le, *p, *Lp;             // p, Lp: (k+1) slots of nx*ny
-    double *part;                   // [ny][NSLOT] row partial sums
+    double *part;                   // [2][NSLOT][ny] block partial sums (phase parity)
     double *hist;                   // optional residual history
     double *rowres;                 // optional per-row final residual
 };
 
-// mutable per-member GCR state, written only by a member's serial section
+// per-member GCR state.  Every block of the member keeps an identical copy in
+// shared memory and advances it with the same deterministic reductions; the
+// global copy holds the initial state (from the host) and the final one.
 struct MemberCtl {
-    int phase, stage, it, nu, base, start, init, status;
-    int arrive;                     // rows finished in the current phase
-    int pad_;
+    int phase, stage, it, nu, base, init, status, pad_;
     double beta, nR, r0, rn_rec, rn_true;
     double alpha[KMAX + 1];
-    double LpLp[KMAX + 1];          // <L p, L p> per physical slot
+    double G[KMAX + 1][KMAX + 1];   // Gram matrix <L p_l, L p_m> of the cycle (logical)
 };
 
 struct GlobalCtl {
-    unsigned count;                 // grid barrier arrivals
-    unsigned gen;                   // grid barrier generation
+    unsigned long long count;       // member barrier arrivals (monotonic)
     int abort;                      // set on a device-side error (timeout)
     int where;                      // diagnostic: step of the abort
 };
@@ -128,8 +133,11 @@ struct alignas(256) SolverBlock {
     GlobalCtl g;
 };
 
-struct EnsembleParams {
-    int n;
+// members of one persistent launch and their block ranges
+struct EnsDesc {
+    int n, grid;
+    int cache_const, cache_state;   // row constants / owner-only vectors in shared memory
+    int cta_begin[MAX_MEMBERS + 1];
     SolverBlock *blk[MAX_MEMBERS];
 };
 

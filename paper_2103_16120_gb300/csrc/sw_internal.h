@@ -7,7 +7,7 @@
 
 namespace sw {
 
-struct EnsembleParams;
+struct EnsDesc;
 
 template <class CT>
 struct OpArgs {
@@ -34,12 +34,13 @@ struct FactorArgs {
 
 cudaError_t launch_faces(const FaceArgs &a, int threads, cudaStream_t s);
 cudaError_t launch_factor(const FactorArgs &a, int threads, cudaStream_t s);
-cudaError_t launch_gcr(int prec, const EnsembleParams &P, int max_nx, int threads, int sms, int total_rows,
-                       cudaStream_t s, int *grid_used);
+size_t gcr_smem_bytes(int prec, int max_nx, int k, int cache_const, int cache_state);
+cudaError_t gcr_occupancy(int prec, int threads, size_t smem, int *blocks_per_sm);
+cudaError_t launch_gcr(int prec, const EnsDesc *Ddev, int grid, int max_nx, int threads, size_t smem, cudaStream_t s);
 cudaError_t launch_operator_f64(const OpArgs<double> &a, const double *x, double *y, int threads, cudaStream_t s);
 cudaError_t launch_operator_f32(const OpArgs<float> &a, const float *x, float *y, int threads, cudaStream_t s);
-cudaError_t launch_precond(int prec, const void *Mdev, int nx, int ny, int nstages, const void *r, void *qout,
-                           int threads, cudaStream_t s);
+cudaError_t launch_precond(int prec, const void *Mdev, int nx, int ny, int nstages, void *qout, int threads,
+                           cudaStream_t s);
 cudaError_t launch_fill(double *p, size_t n, double v, cudaStream_t s);
 size_t member_dev_bytes(int prec);
 

@@ -1,100 +1,203 @@
-// sw_rows.cuh -- per-row work of the elliptic solver: the operator stencil
-// (Eq. 10), the lagged part P^M (Eq. 13), the preconditioner stages and the
-// GCR vector phases.  One thread block processes one latitude row at a time;
-// the rows it reads around j (j-1, j, j+1) are staged in shared memory.
+// sw_rows.cuh -- per-row work of the elliptic solver, one thread block per
+// latitude row: the operator stencil (Eq. 10), the lagged part P^M (Eq. 13)
+// and the preconditioner stages.  The field rows a stencil needs (j-1, j,
+// j+1) are copied into shared memory in one round trip; the row's constant
+// data (face coefficients, zonal factors) and its owner-only vectors (r, L e,
+// p_l, L p_l and a copy of e) live either in shared memory for the whole solve
+// or in global memory, behind the pointers of a RowView.
 #pragma once
 
-#include "sw_common.cuh"
+#include "sw_block.cuh"
 
 namespace sw {
 
-// shared-memory workspace of one block (carved from dynamic shared memory)
+__host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+// ---------------------------------------------------------------------------
+// shared-memory layout of the block (one row at a time)
+//   stg   3 staged rows (policy compute type); also 3 FP64 rows of Phi
+//   raw   mixed policies: the 16-bit / FP32 rows as copied from global memory
+//   sb    one padded row (tridiagonal buffer)
+//   red   reduction / scan scratch
+//   const 11 coefficient rows + 3 padded factor rows of the owned row (optional)
+//   state r, L e, e copy, (k+1) p rows, (k+1) L p rows of the owned row (optional)
+// ---------------------------------------------------------------------------
 template <class Pol>
-struct RowSmem {
-    typedef typename Pol::comp comp;
-    double *s3d;     // 3 rows, FP64 (true residual)
-    comp *s3c;       // 3 rows, policy type (aliases s3d)
-    comp *sb;        // 1 row, tridiagonal buffer
-    double *red;     // NSLOT * nwarps
-    comp *scan;      // 2 * nwarps
-    float *redf;     // nwarps
+__host__ __device__ inline size_t raw_offset(int nx)
+{
+    return al16(3 * (size_t)nx * sizeof(typename Pol::comp));
+}
+
+template <class Pol>
+__host__ __device__ inline size_t sb_offset(int nx)
+{
+    const size_t raw_end = raw_offset<Pol>(nx) + (Pol::kMixed ? al16(3 * (size_t)nx * 4) : 0);
+    const size_t phi3 = al16(3 * (size_t)nx * sizeof(double));
+    return raw_end > phi3 ? raw_end : phi3;
+}
+
+template <class Pol>
+__host__ __device__ inline size_t red_offset(int nx)
+{
+    return sb_offset<Pol>(nx) + al16((size_t)padded_len(nx) * sizeof(typename Pol::comp));
+}
+
+constexpr int RED_WORDS = 32 * (MAX_THREADS / 32);   // scratch values (8 bytes each)
+
+template <class Pol>
+__host__ __device__ inline size_t work_bytes(int nx)
+{
+    return red_offset<Pol>(nx) + al16(RED_WORDS * sizeof(double));
+}
+
+template <class Pol>
+__host__ __device__ inline size_t const_bytes(int nx)
+{
+    return al16(11 * (size_t)nx * sizeof(typename Pol::coef)) + al16(3 * (size_t)padded_len(nx) * sizeof(typename Pol::fac));
+}
+
+template <class Pol>
+__host__ __device__ inline size_t state_bytes(int nx, int k)
+{
+    typedef typename Pol::vec vec;
+    return al16((size_t)nx * sizeof(typename Pol::res)) + al16((size_t)nx * sizeof(vec)) +
+           al16((size_t)nx * sizeof(typename Pol::comp)) + 2 * al16((size_t)(k + 1) * nx * sizeof(vec));
+}
+
+// where the data of one row live
+template <class Pol>
+struct RowView {
+    typedef typename Pol::coef CT;
+    typedef typename Pol::fac FT;
+    typedef typename Pol::vec VT;
+    // constants (coefficient rows unpadded; factor rows padded when fpad)
+    const CT *ax, *cx, *bx, *ay, *cy, *by, *ays, *cys, *bys, *C, *diag;
+    const FT *lf, *invD, *zz;
+    bool fpad;
+    double gam, ec;
+    // owner-only vectors of the row
+    typename Pol::res *r;
+    VT *Le;
+    typename Pol::comp *el;         // copy of the row of e (nullptr: read e itself)
+    VT *pb, *Lpb;                   // slot 0 of p and L p; slot s at + s * vstride
+    size_t vstride;
+};
+
+template <class CT>
+struct RowCoef {
+    const CT *ax, *cx, *bx, *ay, *cy, *by, *ays, *cys, *bys, *C;
 };
 
 template <class Pol>
-__host__ __device__ inline size_t row_smem_bytes(int nx, int threads)
+__device__ __forceinline__ RowCoef<typename Pol::coef> coef_of(const RowView<Pol> &v)
 {
-    size_t nw = threads / 32;
-    size_t a = 3 * (size_t)nx * sizeof(double);
-    size_t b = (size_t)nx * sizeof(typename Pol::comp);
-    size_t c = NSLOT * nw * sizeof(double) + 2 * nw * sizeof(double) + nw * sizeof(float);
-    return ((a + 15) & ~(size_t)15) + ((b + 15) & ~(size_t)15) + c + 64;
+    return {v.ax, v.cx, v.bx, v.ay, v.cy, v.by, v.ays, v.cys, v.bys, v.C};
+}
+
+// constants of row j straight from global memory
+template <class Pol>
+__device__ __forceinline__ void view_const_global(const MemberDev<Pol> &M, int j, RowView<Pol> &v)
+{
+    const size_t row = (size_t)j * M.nx, rs = j > 0 ? row - M.nx : row;
+    v.ax = M.wax + row; v.cx = M.wcx + row; v.bx = M.wbx + row;
+    v.ay = M.way + row; v.cy = M.wcy + row; v.by = M.wby + row;
+    v.ays = M.way + rs; v.cys = M.wcy + rs; v.bys = M.wby + rs;
+    v.C = M.wC + row; v.diag = M.wdiag + row;
+    v.lf = M.lf + row; v.invD = M.invD + row; v.zz = M.zz + row;
+    v.fpad = false;
+    v.gam = M.gam[j]; v.ec = M.ec[j];
+}
+
+// copy row j's constants into the block's cache and point the view there
+template <class Pol>
+__device__ void view_const_cache(const MemberDev<Pol> &M, int j, unsigned char *slot, RowView<Pol> &v)
+{
+    typedef typename Pol::coef CT;
+    typedef typename Pol::fac FT;
+    const int nx = M.nx;
+    RowView<Pol> g;
+    view_const_global(M, j, g);
+    CT *c = (CT *)slot;
+    const CT *src[11] = {g.ax, g.cx, g.bx, g.ay, g.cy, g.by, g.ays, g.cys, g.bys, g.C, g.diag};
+    for (int a = 0; a < 11; ++a)
+        for (int i = threadIdx.x; i < nx; i += blockDim.x) c[a * nx + i] = src[a][i];
+    const int pl = padded_len(nx);
+    FT *f = (FT *)(slot + al16(11 * (size_t)nx * sizeof(CT)));
+    const FT *fs[3] = {g.lf, g.invD, g.zz};
+    for (int a = 0; a < 3; ++a)
+        for (int i = threadIdx.x; i < nx; i += blockDim.x) f[a * pl + pidx(i)] = fs[a][i];
+    v.ax = c; v.cx = c + nx; v.bx = c + 2 * nx; v.ay = c + 3 * nx; v.cy = c + 4 * nx; v.by = c + 5 * nx;
+    v.ays = c + 6 * nx; v.cys = c + 7 * nx; v.bys = c + 8 * nx; v.C = c + 9 * nx; v.diag = c + 10 * nx;
+    v.lf = f; v.invD = f + pl; v.zz = f + 2 * pl;
+    v.fpad = true;
+    v.gam = g.gam; v.ec = g.ec;
 }
 
 template <class Pol>
-__device__ inline RowSmem<Pol> carve_smem(unsigned char *base, int nx)
+__device__ __forceinline__ void view_state_global(const MemberDev<Pol> &M, int j, RowView<Pol> &v)
 {
-    RowSmem<Pol> s;
-    size_t nw = blockDim.x / 32;
-    size_t a = ((3 * (size_t)nx * sizeof(double)) + 15) & ~(size_t)15;
-    size_t b = (((size_t)nx * sizeof(typename Pol::comp)) + 15) & ~(size_t)15;
-    s.s3d = (double *)base;
-    s.s3c = (typename Pol::comp *)base;
-    s.sb = (typename Pol::comp *)(base + a);
-    s.red = (double *)(base + a + b);
-    s.scan = (typename Pol::comp *)(s.red + NSLOT * nw);
-    s.redf = (float *)((double *)s.scan + 2 * nw);
-    return s;
+    const size_t row = (size_t)j * M.nx;
+    v.r = M.r + row;
+    v.Le = M.Le + row;
+    v.el = nullptr;
+    v.pb = M.p + row;
+    v.Lpb = M.Lp + row;
+    v.vstride = (size_t)M.nx * M.ny;
 }
 
-// Stage rows j-1, j, j+1 of a field into s3 (row r of s3 = row j-1+r); the row
-// beyond a pole is the pole row shifted by nx/2.  ld(row, col) loads one value.
-template <class T, class LD>
-__device__ __forceinline__ void stage3(T *s3, int nx, int ny, int j, LD ld)
+template <class Pol>
+__device__ __forceinline__ void view_state_cache(const MemberDev<Pol> &M, unsigned char *slot, RowView<Pol> &v)
 {
-    for (int r = 0; r < 3; ++r) {
-        int jj = j - 1 + r, src = jj, sh = 0;
-        if (jj < 0) { src = 0; sh = nx / 2; }
-        else if (jj >= ny) { src = ny - 1; sh = nx / 2; }
-        for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-            int ii = i + sh;
-            if (ii >= nx) ii -= nx;
-            s3[r * nx + i] = ld(src, ii);
-        }
+    typedef typename Pol::vec VT;
+    const int nx = M.nx;
+    unsigned char *p = slot;
+    v.r = (typename Pol::res *)p; p += al16((size_t)nx * sizeof(typename Pol::res));
+    v.Le = (VT *)p; p += al16((size_t)nx * sizeof(VT));
+    v.el = (typename Pol::comp *)p; p += al16((size_t)nx * sizeof(typename Pol::comp));
+    v.pb = (VT *)p; p += al16((size_t)(M.k + 1) * nx * sizeof(VT));
+    v.Lpb = (VT *)p;
+    v.vstride = nx;
+}
+
+// source row and shift of row jj in [-1, ny] (the row beyond a pole is the
+// pole row shifted by nx/2)
+__device__ __forceinline__ void ghost_row(int jj, int nx, int ny, int &src, int &sh)
+{
+    src = jj; sh = 0;
+    if (jj < 0) { src = 0; sh = nx / 2; }
+    else if (jj >= ny) { src = ny - 1; sh = nx / 2; }
+}
+
+// ---------------------------------------------------------------------------
+// stencils
+// ---------------------------------------------------------------------------
+// y_i = (L x)_i (full) or (P^M x)_i for the whole row from the staged rows
+// S (j-1), X (j), N (j+1); y[pidx(i)] when ypad, else y[i]
+template <class T, class CT>
+__device__ __noinline__ void stencil_row(const T *S, const T *X, const T *N, int nx, int j, int ny,
+                                         const RowCoef<CT> c, bool full, T *y, bool ypad)
+{
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+        const int ie = (i + 1 == nx) ? 0 : i + 1, iw = (i == 0) ? nx - 1 : i - 1;
+        const T xc = X[i], xe = X[ie], xw = X[iw];
+        const T xn = N[i], xne = N[ie], xnw = N[iw];
+        const T xs = S[i], xse = S[ie], xsw = S[iw];
+        const T cx = (T)c.cx[i], cxw = (T)c.cx[iw], bx = (T)c.bx[i], bxw = (T)c.bx[iw];
+        const T ax = full ? (T)c.ax[i] : T(0), axw = full ? (T)c.ax[iw] : T(0);
+        const T ay = (T)c.ay[i], cy = (T)c.cy[i], by = (T)c.by[i];
+        const T ays = (T)c.ays[i], cys = (T)c.cys[i], bys = (T)c.bys[i];
+        const T cc = full ? (T)c.C[i] : T(0);
+        // zonal fluxes through the east (i+1/2) and west (i-1/2) faces
+        T fe = cx * (xn + xne - xs - xse) + bx * (xc + xe) + ax * (xe - xc);
+        T fw = cxw * (xnw + xn - xsw - xs) + bxw * (xw + xc) + axw * (xc - xw);
+        T v = fe - fw;
+        // meridional fluxes through the north (j+1/2) and south (j-1/2)
+        // faces; zero through the pole faces
+        if (j < ny - 1) v += ay * (xn - xc) + cy * (xe + xne - xw - xnw) + by * (xc + xn);
+        if (j > 0) v -= ays * (xc - xs) + cys * (xse + xe - xsw - xw) + bys * (xs + xc);
+        y[ypad ? pidx(i) : i] = v - cc * xc;
     }
     __syncthreads();
-}
-
-// (L x)_ij (full = true) or (P^M x)_ij (full = false) from the staged rows
-// S (j-1), X (j), N (j+1) and the face coefficients of rows j and j-1.
-template <class T, class CT>
-__device__ __forceinline__ T stencil(const T *S, const T *X, const T *N, int i, int nx, int j, int ny,
-                                     const CT *ax, const CT *cx, const CT *bx, const CT *ay,
-                                     const CT *cy, const CT *by, const CT *C, bool full)
-{
-    const int ie = (i + 1 == nx) ? 0 : i + 1;
-    const int iw = (i == 0) ? nx - 1 : i - 1;
-    const size_t row = (size_t)j * nx;
-    const T xc = X[i], xe = X[ie], xw = X[iw];
-    const T xn = N[i], xne = N[ie], xnw = N[iw];
-    const T xs = S[i], xse = S[ie], xsw = S[iw];
-    // zonal fluxes through the east (i+1/2) and west (i-1/2) faces
-    T fe = (T)cx[row + i] * (xn + xne - xs - xse) + (T)bx[row + i] * (xc + xe);
-    T fw = (T)cx[row + iw] * (xnw + xn - xsw - xs) + (T)bx[row + iw] * (xw + xc);
-    if (full) {
-        fe += (T)ax[row + i] * (xe - xc);
-        fw += (T)ax[row + iw] * (xc - xw);
-    }
-    T v = fe - fw;
-    // meridional fluxes through the north (j+1/2) and south (j-1/2) faces;
-    // zero through the pole faces
-    if (j < ny - 1)
-        v += (T)ay[row + i] * (xn - xc) + (T)cy[row + i] * (xe + xne - xw - xnw) + (T)by[row + i] * (xc + xn);
-    if (j > 0) {
-        const size_t rs = row - nx;
-        v -= (T)ay[rs + i] * (xc - xs) + (T)cy[rs + i] * (xse + xe - xsw - xw) + (T)by[rs + i] * (xs + xc);
-    }
-    if (full) v -= (T)C[row + i] * xc;
-    return v;
 }
 
 template <class Pol>
@@ -103,134 +206,202 @@ __device__ __forceinline__ bool in_band(const MemberDev<Pol> &M, int j)
     return Pol::kMixed && (j < M.band || j >= M.ny - M.band);
 }
 
-// value (i) of row j of a preconditioner field (q or e): FP64 for the FP64
-// policy; FP32 on pole-band rows or 16-bit times the row scale otherwise.
+template <class Pol>
+__device__ __forceinline__ float q_scale(const MemberDev<Pol> &M, const float *sc, int j)
+{
+    if constexpr (Pol::kMixed) return in_band(M, j) ? 1.f : __ldcg(sc + j);
+    else return 1.f;
+}
+
+// value (i) of row j of a preconditioner field read straight from global
+// memory (rows without a shared-memory copy)
 template <class Pol>
 __device__ __forceinline__ typename Pol::comp q_load(const MemberDev<Pol> &M, const typename Pol::q16 *h,
                                                      const float *f32, float sc, int j, int i)
 {
     const size_t id = (size_t)j * M.nx + i;
     if constexpr (!Pol::kMixed) {
-        return ldcg(h + id);
+        return __ldcg(h + id);
     } else {
-        if (in_band(M, j)) return ldcg(f32 + id);
-        return q_to_f(ldcg(h + id)) * sc;
+        if (in_band(M, j)) return __ldcg(f32 + id);
+        return q_to_f(h[id]) * sc;
     }
 }
 
+// stage rows j-1, j, j+1 of a preconditioner field into stg: the three source
+// rows are copied as they are (one round trip), then converted with their
+// row scales and the pole shift in shared memory
 template <class Pol>
-__device__ __forceinline__ float q_scale(const MemberDev<Pol> &M, const float *sc, int j)
+__device__ __noinline__ void stage3_q(unsigned char *ws, const MemberDev<Pol> &M, const typename Pol::q16 *h,
+                                      const float *f32, const float *sc, int j)
 {
-    if constexpr (Pol::kMixed) return in_band(M, j) ? 1.f : ldcg(sc + j);
-    else return 1.f;
-}
-
-template <class Pol>
-__device__ __forceinline__ void stage3_q(typename Pol::comp *s3, const MemberDev<Pol> &M,
-                                         const typename Pol::q16 *h, const float *f32, const float *sc, int j)
-{
+    typedef typename Pol::comp comp;
+    typedef typename Pol::q16 qt;
     const int nx = M.nx, ny = M.ny;
+    comp *stg = (comp *)ws;
+    int src[3], sh[3];
+    if constexpr (!Pol::kMixed) {
+        // FP64: straight into the stage, the pole shift as two half-row copies
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            ghost_row(j - 1 + r, nx, ny, src[r], sh[r]);
+            const qt *sr = h + (size_t)src[r] * nx;
+            comp *d = stg + (size_t)r * nx;
+            if (sh[r] == 0) {
+                row_copy_issue(d, sr, nx * (int)sizeof(qt));
+            } else {
+                row_copy_issue(d, sr + sh[r], (nx - sh[r]) * (int)sizeof(qt));
+                row_copy_issue(d + (nx - sh[r]), sr, sh[r] * (int)sizeof(qt));
+            }
+        }
+        row_copy_wait();
+        return;
+    }
+    unsigned char *raw = ws + raw_offset<Pol>(nx);
+    const size_t rs = (size_t)nx * 4;   // raw row stride
+    bool band[3];
+#pragma unroll
     for (int r = 0; r < 3; ++r) {
-        int jj = j - 1 + r, src = jj, sh = 0;
-        if (jj < 0) { src = 0; sh = nx / 2; }
-        else if (jj >= ny) { src = ny - 1; sh = nx / 2; }
-        const float s = q_scale(M, sc, src);
+        ghost_row(j - 1 + r, nx, ny, src[r], sh[r]);
+        band[r] = in_band(M, src[r]);
+        const size_t off = (size_t)src[r] * nx;
+        if (band[r]) row_copy_issue(raw + r * rs, f32 + off, nx * 4);
+        else row_copy_issue(raw + r * rs, h + off, nx * (int)sizeof(qt));
+    }
+    float s[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) s[r] = q_scale(M, sc, src[r]);
+    row_copy_wait();
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        const qt *rq = (const qt *)(raw + r * rs);
+        const float *rf = (const float *)(raw + r * rs);
         for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-            int ii = i + sh;
+            int ii = i + sh[r];
             if (ii >= nx) ii -= nx;
-            s3[r * nx + i] = q_load(M, h, f32, s, src, ii);
+            stg[r * nx + i] = band[r] ? rf[ii] : q_to_f(rq[ii]) * s[r];
         }
     }
     __syncthreads();
 }
 
-// store row j of a preconditioner field from sb (16-bit storage gets a
-// power-of-two row scale so that the stored magnitudes are <= 1)
+// store row j of a preconditioner field from the padded buffer sb (16-bit
+// storage gets a power-of-two row scale so the stored magnitudes are <= 1);
+// el (optional) receives the values as stored
 template <class Pol>
-__device__ __forceinline__ void q_store_row(const MemberDev<Pol> &M, typename Pol::q16 *h, float *f32,
-                                            float *sc, int j, const typename Pol::comp *sb, float *redf)
+__device__ __noinline__ void q_store_row(const MemberDev<Pol> &M, typename Pol::q16 *h, float *f32, float *sc,
+                                         int j, const typename Pol::comp *sb, typename Pol::comp *el,
+                                         float *scratch)
 {
+    typedef typename Pol::comp comp;
     const int nx = M.nx;
     const size_t row = (size_t)j * nx;
     if constexpr (!Pol::kMixed) {
-        for (int i = threadIdx.x; i < nx; i += blockDim.x) h[row + i] = sb[i];
+        for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+            const comp v = sb[pidx(i)];
+            h[row + i] = v;
+            if (el) el[i] = v;
+        }
     } else {
         if (in_band(M, j)) {
-            for (int i = threadIdx.x; i < nx; i += blockDim.x) f32[row + i] = sb[i];
-            return;
+            for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+                const comp v = sb[pidx(i)];
+                f32[row + i] = v;
+                if (el) el[i] = v;
+            }
+        } else {
+            float m = 0.f;
+            for (int i = threadIdx.x; i < nx; i += blockDim.x) m = fmaxf(m, fabsf(sb[pidx(i)]));
+            m = block_max(m, scratch);
+            float s = 1.f;
+            if (m > 0.f && m <= 3.0e38f) { int e; frexpf(m, &e); s = ldexpf(1.f, e); }
+            else if (!(m <= 3.0e38f)) s = m;        // NaN / Inf: propagate
+            const float inv = 1.f / s;              // exact: s is a power of two
+            for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+                const typename Pol::q16 q = f_to_q<typename Pol::q16>(sb[pidx(i)] * inv);
+                h[row + i] = q;
+                if (el) el[i] = q_to_f(q) * s;
+            }
+            if (threadIdx.x == 0) sc[j] = s;
         }
-        float m = 0.f;
-        for (int i = threadIdx.x; i < nx; i += blockDim.x) m = fmaxf(m, fabsf(sb[i]));
-        m = block_max(m, redf);
-        float s = 1.f;
-        if (m > 0.f && m <= 3.0e38f) { int e; frexpf(m, &e); s = ldexpf(1.f, e); }
-        else if (!(m <= 3.0e38f)) s = m;        // NaN / Inf: propagate
-        const float inv = 1.f / s;              // exact: s is a power of two
-        for (int i = threadIdx.x; i < nx; i += blockDim.x) h[row + i] = f_to_q<typename Pol::q16>(sb[i] * inv);
-        if (threadIdx.x == 0) sc[j] = s;
     }
+    __syncthreads();
 }
 
 // pointwise first Richardson stage input from the residual value rv:
 // option 0: r; 1: r/D; 2: omega r/D (q_1 with q_0 = 0); 3: -eta r (then T^{-1})
 template <class Pol>
-__device__ __forceinline__ typename Pol::comp stage0_input(const MemberDev<Pol> &M, double eta,
-                                                           typename Pol::comp rv, size_t id)
+__device__ __forceinline__ typename Pol::comp stage0_input(const MemberDev<Pol> &M, const RowView<Pol> &v,
+                                                           typename Pol::comp eta, typename Pol::comp rv, int i)
 {
     typedef typename Pol::comp comp;
     switch (M.pc) {
     case 0: return rv;
-    case 1: return rv / (comp)M.wdiag[id];
-    case 2: return (comp)M.omega * rv / (comp)M.wdiag[id];
-    default: return -(comp)eta * rv;
+    case 1: return rv / (comp)v.diag[i];
+    case 2: return (comp)M.omega * rv / (comp)v.diag[i];
+    default: return -eta * rv;
     }
+}
+
+template <class Pol>
+__device__ __forceinline__ void trisolve_view(typename Pol::comp *sb, int nx, const RowView<Pol> &v,
+                                              typename Pol::comp *sm)
+{
+    typedef typename Pol::comp comp;
+    if (v.fpad) trisolve_block<comp, typename Pol::fac, true>(sb, nx, v.lf, v.invD, v.zz, (comp)v.gam, (comp)v.ec, sm);
+    else trisolve_block<comp, typename Pol::fac, false>(sb, nx, v.lf, v.invD, v.zz, (comp)v.gam, (comp)v.ec, sm);
 }
 
 // finish the first preconditioner stage of row j (sb holds stage0_input):
-// option 3 solves the zonal system; the result goes to e (single stage) or qa.
+// option 3 solves the zonal system; the result goes to e (single stage) or qa
 template <class Pol>
-__device__ void stage0_finish(const MemberDev<Pol> &M, int j, RowSmem<Pol> &sm)
+__device__ void stage0_finish(const MemberDev<Pol> &M, const RowView<Pol> &v, int j, unsigned char *ws)
 {
     typedef typename Pol::comp comp;
+    comp *sb = (comp *)(ws + sb_offset<Pol>(M.nx));
+    comp *sm = (comp *)(ws + red_offset<Pol>(M.nx));
     __syncthreads();
-    const size_t row = (size_t)j * M.nx;
-    if (M.pc == 3)
-        trisolve_row<comp, typename Pol::fac>(sm.sb, M.nx, M.lf + row, M.invD + row, M.zz + row,
-                                              (comp)M.gam[j], (comp)M.ec[j], sm.scan);
-    if (M.nstages == 1) q_store_row(M, M.e, M.e32, M.e_s, j, sm.sb, sm.redf);
-    else q_store_row(M, M.qa, M.qa32, M.qa_s, j, sm.sb, sm.redf);
-    __syncthreads();
+    SW_TRACE(401);
+    if (M.pc == 3) trisolve_view(sb, M.nx, v, sm);
+    SW_TRACE(402);
+    if (M.nstages == 1) q_store_row(M, M.e, M.e32, M.e_s, j, sb, v.el, (float *)sm);
+    else q_store_row(M, M.qa, M.qa32, M.qa_s, j, sb, (comp *)nullptr, (float *)sm);
 }
 
-// preconditioner stage mu >= 1 of row j: reads q_mu (rows j-1..j+1) from
-// `in`, writes q_{mu+1} to `out`.
+// preconditioner stage mu >= 1 of row j: reads q_mu (rows j-1..j+1), writes
+// q_{mu+1} (the last stage writes e).
 //   option 3 (Eq. 13): [I - eta (P^Z - P^H)] q_{mu+1} = q_mu + eta (P^M q_mu - r)
 //   option 2:          q_{mu+1} = q_mu + omega D^{-1} (r - L q_mu)
-template <class Pol, class RT>
-__device__ void precond_stage(const MemberDev<Pol> &M, double eta, int j, RowSmem<Pol> &sm,
-                              const typename Pol::q16 *in_h, const float *in_f, const float *in_s,
-                              const RT *r,
-                              typename Pol::q16 *out_h, float *out_f, float *out_s)
+template <class Pol>
+__device__ void precond_stage(const MemberDev<Pol> &M, const RowView<Pol> &v, typename Pol::comp eta, int mu,
+                              int j, unsigned char *ws)
 {
     typedef typename Pol::comp comp;
     const int nx = M.nx, ny = M.ny;
-    const size_t row = (size_t)j * nx;
-    stage3_q(sm.s3c, M, in_h, in_f, in_s, j);
-    const comp *S = sm.s3c, *X = sm.s3c + nx, *N = sm.s3c + 2 * nx;
+    const bool last = (mu == M.nstages - 1);
+    const typename Pol::q16 *ih = (mu & 1) ? M.qa : M.qb;
+    const float *if32 = (mu & 1) ? M.qa32 : M.qb32;
+    const float *is = (mu & 1) ? M.qa_s : M.qb_s;
+    typename Pol::q16 *oh = last ? M.e : ((mu & 1) ? M.qb : M.qa);
+    float *of32 = last ? M.e32 : ((mu & 1) ? M.qb32 : M.qa32);
+    float *os = last ? M.e_s : ((mu & 1) ? M.qb_s : M.qa_s);
+    comp *stg = (comp *)ws;
+    comp *sb = (comp *)(ws + sb_offset<Pol>(nx));
+    comp *sm = (comp *)(ws + red_offset<Pol>(nx));
+    stage3_q(ws, M, ih, if32, is, j);
+    SW_TRACE(301);
+    const comp *S = stg, *X = stg + nx, *N = stg + 2 * nx;
     const bool opt3 = (M.pc == 3);
+    stencil_row<comp, typename Pol::coef>(S, X, N, nx, j, ny, coef_of(v), !opt3, sb, true);
     for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-        comp rv = (comp)ldcg(r + row + i);
-        comp v = stencil<comp, typename Pol::coef>(S, X, N, i, nx, j, ny, M.wax, M.wcx, M.wbx, M.way,
-                                                   M.wcy, M.wby, M.wC, !opt3);
-        if (opt3) sm.sb[i] = X[i] + (comp)eta * (v - rv);
-        else sm.sb[i] = X[i] + (comp)M.omega * (rv - v) / (comp)M.wdiag[row + i];
+        const comp s = sb[pidx(i)], rv = (comp)v.r[i], xv = X[i];
+        sb[pidx(i)] = opt3 ? xv + eta * (s - rv) : xv + (comp)M.omega * (rv - s) / (comp)v.diag[i];
     }
     __syncthreads();
-    if (opt3)
-        trisolve_row<comp, typename Pol::fac>(sm.sb, nx, M.lf + row, M.invD + row, M.zz + row,
-                                              (comp)M.gam[j], (comp)M.ec[j], sm.scan);
-    q_store_row(M, out_h, out_f, out_s, j, sm.sb, sm.redf);
-    __syncthreads();
+    SW_TRACE(302);
+    if (opt3) trisolve_view(sb, nx, v, sm);
+    SW_TRACE(303);
+    q_store_row(M, oh, of32, os, j, sb, last ? v.el : (comp *)nullptr, (float *)sm);
 }
 
 } // namespace sw

@@ -1,22 +1,38 @@
 // sw_solver.cu -- preconditioned GCR(k) (Sec. 2.3) as one persistent,
 // cooperative kernel per solve or ensemble of solves, plus the standalone
-// operator and preconditioner kernels behind sw_operator_apply and
-// sw_precond_apply.
+// preconditioner and operator kernels behind sw_precond_apply and
+// sw_operator_apply.
 //
-// The GCR iteration is a state machine per member.  Every step of the
-// persistent kernel runs one phase for every active member, one latitude row
-// per block at a time; after a member's last row of the phase, the block that
-// finished it (found with an arrival counter) reduces the member's row
-// partial sums in a fixed order and advances its state.  A bounded grid
-// barrier separates the steps.  Phases (the text's step numbers in brackets):
-//   PH_TRUE  r = L(Phi) - R in FP64 [step 1 / residual check], ||r||^2, first
-//            preconditioner stage
-//   PH_BETA  Phi += beta p_nu, r += beta L p_nu [step 2], ||r||^2, first
-//            preconditioner stage of the new r [step 3]
-//   PH_PREC  Richardson stage mu >= 1 (needs neighbour rows) [step 3]
-//   PH_LE    L(e) and <L e, L p_l> [step 3]; at a (re)start p_0 = e
-//   PH_UPD   p_{nu+1}, L p_{nu+1}, <L p, L p>, <r, L p> [step 4]
-//   PH_ZERO  Phi = 0 for a zero right-hand side
+// Layout of the work.  Each member (one elliptic problem) owns a group of
+// thread blocks for the whole solve; each block owns latitude rows (one row
+// when the member's rows fit the co-resident blocks), so the row's face
+// coefficients, zonal factors and owner-only vectors (r, L e, p_l, L p_l) can
+// stay in shared memory between phases.  Only what other rows read (the
+// preconditioner fields q and e, and Phi) goes through global memory, and the
+// rows a block needs from there are copied in with one round trip per phase.
+//
+// The GCR iteration is a state machine whose state every block of the member
+// holds in shared memory.  After each phase the block sums its rows' partial
+// sums in a fixed order and publishes them; the member's blocks meet at a
+// bounded barrier (a monotonic counter with release/acquire semantics); every
+// block then adds the published block sums in the same fixed order and applies
+// the same transition, so all copies of the state agree.
+//
+// Phases (the text's algorithmic steps in brackets):
+//   PH_TRUE  r = L(Phi) - R in FP64 [step 1 / final check], ||r||^2, and the
+//            first preconditioner stage of r
+//   PH_PREC  Richardson stage mu >= 1, which needs neighbour rows [step 3]
+//   PH_LE    L(e) and the inner products <Le,Le>, <r,Le>, <Le,Lp_l>,
+//            <r,Lp_l> [steps 3-4]
+//   PH_UB    p_{nu+1} = e + sum alpha_l p_l, Lp_{nu+1} = Le + sum alpha_l Lp_l
+//            [step 4], Phi += beta p_{nu+1}, r += beta Lp_{nu+1} [step 2],
+//            ||r||^2, <Lp_{nu+1}, Lp_m>, and the first preconditioner stage of
+//            the new r [step 3]
+// The coefficients alpha_l = -<Le,Lp_l>/<Lp_l,Lp_l> are those of the text;
+// beta = -<r,Lp_{nu+1}>/<Lp_{nu+1},Lp_{nu+1}> is evaluated before Lp_{nu+1}
+// exists, from the PH_LE inner products and the Gram matrix of the cycle's
+// directions (the same value, a different rounding), so the update and the
+// step share one pass: three phases per iteration.
 #include "sw_rows.cuh"
 #include "sw_internal.h"
 
@@ -31,43 +47,7 @@ __device__ __forceinline__ unsigned long long gtimer()
     return t;
 }
 
-__device__ __forceinline__ unsigned vload(const unsigned *p) { return *(const volatile unsigned *)p; }
 __device__ __forceinline__ int vload(const int *p) { return *(const volatile int *)p; }
-
-// Bounded grid barrier (all blocks co-resident: cooperative launch).
-// Returns false if the wait ran out or another block gave up.
-__device__ bool grid_barrier(GlobalCtl *G, int step)
-{
-    __shared__ int s_ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int ok = 1;
-        unsigned gen0 = vload(&G->gen);
-        __threadfence();
-        unsigned old = atomicAdd(&G->count, 1u);
-        if (old == gridDim.x - 1) {
-            atomicExch(&G->count, 0u);
-            __threadfence();
-            atomicAdd(&G->gen, 1u);
-        } else {
-            const unsigned long long t0 = gtimer();
-            while (vload(&G->gen) == gen0) {
-                if (vload(&G->abort)) { ok = 0; break; }
-                if (gtimer() - t0 > WAIT_LIMIT_NS) {
-                    if (atomicExch(&G->abort, 1) == 0) G->where = step;
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(40);
-            }
-        }
-        __threadfence();
-        if (vload(&G->abort)) ok = 0;
-        s_ok = ok;
-    }
-    __syncthreads();
-    return s_ok != 0;
-}
 
 template <class Pol>
 __device__ __forceinline__ const MemberDev<Pol> *mdev(SolverBlock *b) { return (const MemberDev<Pol> *)b->dev; }
@@ -81,381 +61,418 @@ __device__ __forceinline__ void copy_in(T *dst, const T *src)
     static_assert(sizeof(T) % 4 == 0, "");
     const int *s = (const int *)src;
     int *d = (int *)dst;
-    for (int k = threadIdx.x; k < (int)(sizeof(T) / 4); k += blockDim.x) d[k] = ldcg(s + k);
+    for (int k = threadIdx.x; k < (int)(sizeof(T) / 4); k += blockDim.x) d[k] = __ldcg(s + k);
 }
 
-// ---------------------------------------------------------------------------
-// phases on one row j of member M (state snapshot c)
-// ---------------------------------------------------------------------------
-template <class Pol>
-__device__ void phase_true(const MemberDev<Pol> &M, const MemberCtl &c, double eta, int j, RowSmem<Pol> &sm)
+// partial-sum slots of each phase (see NSLOT)
+__device__ __forceinline__ int phase_slots(int phase, int nd, int *slot)
 {
-    typedef typename Pol::comp comp;
-    const int nx = M.nx, ny = M.ny;
-    const size_t row = (size_t)j * nx;
-    const double *phi = M.phi;
-    stage3<double>(sm.s3d, nx, ny, j, [&](int jj, int ii) { return ldcg(phi + (size_t)jj * nx + ii); });
-    const double *S = sm.s3d, *X = sm.s3d + nx, *N = sm.s3d + 2 * nx;
-    double acc[2] = {0.0, 0.0};
-    // the staged rows alias sb's neighbour region only for the FP64 policy's
-    // s3c, which is not used here; sb is a separate region
-    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-        double Rv = M.R[row + i];
-        double rv = stencil<double, double>(S, X, N, i, nx, j, ny, M.ax, M.cx, M.bx, M.ay, M.cy, M.by, M.C, true) - Rv;
-        typename Pol::res rs = (typename Pol::res)rv;
-        M.r[row + i] = rs;
-        acc[0] += rv * rv;
-        acc[1] += Rv * Rv;
-        sm.sb[i] = stage0_input(M, eta, (comp)rs, row + i);
-    }
-    block_sum(acc, 2, sm.red);
-    if (threadIdx.x == 0) {
-        M.part[(size_t)j * NSLOT + S_RR] = acc[0];
-        M.part[(size_t)j * NSLOT + S_R2] = acc[1];
-    }
-    stage0_finish(M, j, sm);
-}
-
-template <class Pol>
-__device__ void phase_beta(const MemberDev<Pol> &M, const MemberCtl &c, double eta, int j, RowSmem<Pol> &sm)
-{
-    typedef typename Pol::comp comp;
-    const int nx = M.nx;
-    const size_t row = (size_t)j * nx;
-    const size_t N = (size_t)nx * M.ny;
-    const int s = phys_slot(c, M.k, c.nu);
-    const typename Pol::vec *p = M.p + s * N, *Lp = M.Lp + s * N;
-    const double beta = c.beta;
-    double acc[1] = {0.0};
-    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-        const size_t id = row + i;
-        double pv = (double)ldcg(p + id), lv = (double)ldcg(Lp + id);
-        M.phi[id] = ldcg(M.phi + id) + beta * pv;
-        typename Pol::res rs = (typename Pol::res)((double)ldcg(M.r + id) + beta * lv);
-        M.r[id] = rs;
-        acc[0] += (double)rs * (double)rs;
-        sm.sb[i] = stage0_input(M, eta, (comp)rs, id);
-    }
-    block_sum(acc, 1, sm.red);
-    if (threadIdx.x == 0) M.part[(size_t)j * NSLOT + S_RR] = acc[0];
-    stage0_finish(M, j, sm);
-}
-
-template <class Pol>
-__device__ void phase_prec(const MemberDev<Pol> &M, const MemberCtl &c, double eta, int j, RowSmem<Pol> &sm)
-{
-    const int mu = c.stage;     // 1 .. nstages-1
-    const bool last = (mu == M.nstages - 1);
-    const typename Pol::q16 *ih = (mu & 1) ? M.qa : M.qb;
-    const float *if32 = (mu & 1) ? M.qa32 : M.qb32;
-    const float *is = (mu & 1) ? M.qa_s : M.qb_s;
-    typename Pol::q16 *oh = last ? M.e : ((mu & 1) ? M.qb : M.qa);
-    float *of32 = last ? M.e32 : ((mu & 1) ? M.qb32 : M.qa32);
-    float *os = last ? M.e_s : ((mu & 1) ? M.qb_s : M.qa_s);
-    precond_stage(M, eta, j, sm, ih, if32, is, M.r, oh, of32, os);
-}
-
-template <class Pol>
-__device__ void phase_le(const MemberDev<Pol> &M, const MemberCtl &c, int j, RowSmem<Pol> &sm)
-{
-    typedef typename Pol::comp comp;
-    typedef typename Pol::vec vec;
-    const int nx = M.nx, ny = M.ny;
-    const size_t row = (size_t)j * nx;
-    const size_t N = (size_t)nx * ny;
-    stage3_q(sm.s3c, M, M.e, M.e32, M.e_s, j);
-    const comp *S = sm.s3c, *X = sm.s3c + nx, *Nn = sm.s3c + 2 * nx;
-    double acc[KMAX + 1];
-    if (c.start) {
-        const int s0 = phys_slot(c, M.k, 0);
-        vec *p = M.p + s0 * N, *Lp = M.Lp + s0 * N;
-        acc[0] = acc[1] = 0.0;
-        for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-            comp le = stencil<comp, typename Pol::coef>(S, X, Nn, i, nx, j, ny, M.wax, M.wcx, M.wbx, M.way,
-                                                        M.wcy, M.wby, M.wC, true);
-            vec lv = (vec)le;
-            p[row + i] = (vec)X[i];
-            Lp[row + i] = lv;
-            acc[0] += (double)lv * (double)lv;
-            acc[1] += (double)ldcg(M.r + row + i) * (double)lv;
-        }
-        block_sum(acc, 2, sm.red);
-        if (threadIdx.x == 0) {
-            M.part[(size_t)j * NSLOT + S_LPLP] = acc[0];
-            M.part[(size_t)j * NSLOT + S_RLP] = acc[1];
-        }
-    } else {
-        const int nd = c.nu + 1;
-        for (int l = 0; l < nd; ++l) acc[l] = 0.0;
-        for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-            comp le = stencil<comp, typename Pol::coef>(S, X, Nn, i, nx, j, ny, M.wax, M.wcx, M.wbx, M.way,
-                                                        M.wcy, M.wby, M.wC, true);
-            vec lv = (vec)le;
-            M.Le[row + i] = lv;
-            for (int l = 0; l < nd; ++l) {
-                const vec *Lpl = M.Lp + phys_slot(c, M.k, l) * N;
-                acc[l] += (double)lv * (double)ldcg(Lpl + row + i);
-            }
-        }
-        block_sum(acc, nd, sm.red);
-        if (threadIdx.x == 0)
-            for (int l = 0; l < nd; ++l) M.part[(size_t)j * NSLOT + S_DOT0 + l] = acc[l];
-    }
-    __syncthreads();
-}
-
-template <class Pol>
-__device__ void phase_upd(const MemberDev<Pol> &M, const MemberCtl &c, int j, RowSmem<Pol> &sm)
-{
-    typedef typename Pol::comp comp;
-    typedef typename Pol::vec vec;
-    const int nx = M.nx;
-    const size_t row = (size_t)j * nx;
-    const size_t N = (size_t)nx * M.ny;
-    const int nd = c.nu + 1;
-    const int sn = phys_slot(c, M.k, nd);
-    vec *pn = M.p + sn * N, *Lpn = M.Lp + sn * N;
-    const float esc = q_scale(M, M.e_s, j);
-    double acc[2] = {0.0, 0.0};
-    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-        const size_t id = row + i;
-        comp pv = q_load(M, M.e, M.e32, esc, j, i);
-        comp lv = (comp)ldcg(M.Le + id);
-        for (int l = 0; l < nd; ++l) {
-            const size_t off = phys_slot(c, M.k, l) * N + id;
-            comp a = (comp)c.alpha[l];
-            pv += a * (comp)ldcg(M.p + off);
-            lv += a * (comp)ldcg(M.Lp + off);
-        }
-        vec ps = (vec)pv, ls = (vec)lv;
-        pn[id] = ps;
-        Lpn[id] = ls;
-        acc[0] += (double)ls * (double)ls;
-        acc[1] += (double)ldcg(M.r + id) * (double)ls;
-    }
-    block_sum(acc, 2, sm.red);
-    if (threadIdx.x == 0) {
-        M.part[(size_t)j * NSLOT + S_LPLP] = acc[0];
-        M.part[(size_t)j * NSLOT + S_RLP] = acc[1];
-    }
-}
-
-template <class Pol>
-__device__ void phase_zero(const MemberDev<Pol> &M, int j)
-{
-    const size_t row = (size_t)j * M.nx;
-    for (int i = threadIdx.x; i < M.nx; i += blockDim.x) M.phi[row + i] = 0.0;
-    if (threadIdx.x == 0) M.part[(size_t)j * NSLOT + S_RR] = 0.0;
-}
-
-// ---------------------------------------------------------------------------
-// serial section of one member: reduce its row partials (fixed order) and
-// advance its state.  Run by the block that finished the member's last row.
-// ---------------------------------------------------------------------------
-template <class Pol>
-__device__ void member_serial(SolverBlock *B, const MemberDev<Pol> &M, MemberCtl &c, RowSmem<Pol> &sm)
-{
-    int s0 = 0, ns = 0;
-    switch (c.phase) {
-    case PH_TRUE: s0 = S_RR; ns = c.init ? 2 : 1; break;
-    case PH_BETA: s0 = S_RR; ns = 1; break;
-    case PH_LE: if (c.start) { s0 = S_LPLP; ns = 2; } else { s0 = S_DOT0; ns = c.nu + 1; } break;
-    case PH_UPD: s0 = S_LPLP; ns = 2; break;
+    int ns = 0;
+    switch (phase) {
+    case PH_TRUE: case PH_ZERO: slot[0] = S_A; slot[1] = S_B; ns = 2; break;
+    case PH_UB:
+        slot[0] = S_A; slot[1] = S_B; ns = 2;
+        for (int l = 0; l < nd; ++l) slot[ns++] = S_C0 + l;
+        break;
+    case PH_LE:
+        slot[0] = S_A; slot[1] = S_B; ns = 2;
+        for (int l = 0; l < nd; ++l) slot[ns++] = S_C0 + l;
+        for (int l = 0; l < nd; ++l) slot[ns++] = S_T0 + l;
+        break;
     default: break;
     }
-    double acc[KMAX + 1];
-    for (int s = 0; s < ns; ++s) acc[s] = 0.0;
-    for (int r = threadIdx.x; r < M.ny; r += blockDim.x)
-        for (int s = 0; s < ns; ++s) acc[s] += ldcg(M.part + (size_t)r * NSLOT + s0 + s);
-    if (ns > 0) block_sum(acc, ns, sm.red);
-    __shared__ int s_rowres;
-    if (threadIdx.x == 0) {
-        const int k = M.k;
-        bool done = false;
-        int ph = c.phase;
-        auto to_precond = [&]() { c.stage = 1; c.phase = (M.nstages > 1) ? PH_PREC : PH_LE; };
-        auto finish = [&](int st) { c.status = st; done = true; };
-        switch (ph) {
-        case PH_TRUE: {
-            double rn = sqrt(acc[0]);
-            if (c.init) {
-                c.init = 0;
-                c.nR = sqrt(acc[1]);
-                c.r0 = rn;
-                c.rn_true = c.rn_rec = rn;
-                if (M.hist) M.hist[0] = c.nR > 0.0 ? rn / c.nR : 0.0;
-                if (c.nR == 0.0) { c.phase = PH_ZERO; break; }
-                if (!isfinite(rn) || !isfinite(c.nR)) { finish(ST_NONFINITE); break; }
-                if (rn <= M.tol * c.nR && M.min_iters <= 0) { finish(ST_OK); break; }
-                c.start = 1;
-                to_precond();
-            } else {
-                c.rn_true = rn;
-                if (M.hist) M.hist[c.it] = rn / c.nR;
-                if (!isfinite(rn)) { finish(ST_NONFINITE); break; }
-                if (rn <= M.tol * c.nR && c.it >= M.min_iters) { finish(ST_OK); break; }
-                if (c.it >= M.max_iters) { finish(ST_NOT_CONVERGED); break; }
-                to_precond();
-            }
-            break;
-        }
-        case PH_PREC:
-            c.stage += 1;
-            if (c.stage >= M.nstages) c.phase = PH_LE;
-            break;
-        case PH_LE:
-            if (c.start) {
-                double lplp = acc[0], rlp = acc[1];
-                if (!(lplp > 0.0) || !isfinite(lplp)) { finish(ST_BREAKDOWN); break; }
-                c.LpLp[phys_slot(c, k, 0)] = lplp;
-                c.beta = -rlp / lplp;
-                c.start = 0;
-                c.nu = 0;
-                c.phase = PH_BETA;
-            } else {
-                for (int l = 0; l <= c.nu; ++l) c.alpha[l] = -acc[l] / c.LpLp[phys_slot(c, k, l)];
-                c.phase = PH_UPD;
-            }
-            break;
-        case PH_UPD: {
-            double lplp = acc[0], rlp = acc[1];
-            if (!(lplp > 0.0) || !isfinite(lplp)) { finish(ST_BREAKDOWN); break; }
-            c.LpLp[phys_slot(c, k, c.nu + 1)] = lplp;
-            c.beta = -rlp / lplp;
-            c.nu += 1;
-            if (c.nu == k) { c.base = phys_slot(c, k, k); c.nu = 0; }
-            c.phase = PH_BETA;
-            break;
-        }
-        case PH_BETA: {
-            c.it += 1;
-            double rn = sqrt(acc[0]);
-            c.rn_rec = rn;
-            if (M.hist) M.hist[c.it] = rn / c.nR;
-            if (!isfinite(rn)) { finish(ST_NONFINITE); break; }
-            if ((rn <= M.tol * c.nR && c.it >= M.min_iters) || (M.ru_every > 0 && c.it % M.ru_every == 0) ||
-                c.it >= M.max_iters)
-                c.phase = PH_TRUE;
-            else
-                to_precond();
-            break;
-        }
-        case PH_ZERO:
-            c.rn_true = c.rn_rec = 0.0;
-            finish(ST_OK);
-            break;
-        default: break;
-        }
-        s_rowres = (done && (ph == PH_TRUE || ph == PH_ZERO) && M.rowres) ? 1 : 0;
-        if (done) c.phase = PH_DONE;
-        // publish the new state
-        MemberCtl *g = &B->ctl;
-        c.arrive = 0;
-        const int *src = (const int *)&c;
-        int *dst = (int *)g;
-        for (int w = 0; w < (int)(sizeof(MemberCtl) / 4); ++w) dst[w] = src[w];
-        __threadfence();
+    return ns;
+}
+
+// ---------------------------------------------------------------------------
+// phases on one row j (one block).  Each thread adds its share of the phase's
+// inner products to part[slot]; the caller sums them over the block.
+// ---------------------------------------------------------------------------
+template <class Pol>
+__device__ void phase_true(const MemberDev<Pol> &M, const RowView<Pol> &v, typename Pol::comp eta, int j,
+                           unsigned char *ws, typename Acc<Pol>::type (&part)[NSLOT])
+{
+    typedef typename Pol::comp comp;
+    const int nx = M.nx, ny = M.ny;
+    const size_t row = (size_t)j * nx;
+    comp *sb = (comp *)(ws + sb_offset<Pol>(nx));
+    // FP64 coefficients: the policy's own (FP64 policy) or the FP64 copies
+    RowCoef<double> c;
+    if constexpr (Pol::kMixed) {
+        const size_t rs = j > 0 ? row - nx : row;
+        c = {M.ax + row, M.cx + row, M.bx + row, M.ay + row, M.cy + row, M.by + row,
+             M.ay + rs, M.cy + rs, M.by + rs, M.C + row};
+    } else {
+        c = coef_of(v);
     }
-    __syncthreads();
-    if (s_rowres)
-        for (int r = threadIdx.x; r < M.ny; r += blockDim.x)
-            M.rowres[r] = sqrt(ldcg(M.part + (size_t)r * NSLOT + S_RR));
-    __syncthreads();
+    // the three Phi rows (FP64), unshifted, into the stage + raw region
+    double *ph = (double *)ws;
+    int src[3], sh[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        ghost_row(j - 1 + r, nx, ny, src[r], sh[r]);
+        row_copy_issue(ph + (size_t)r * nx, M.phi + (size_t)src[r] * nx, nx * 8);
+    }
+    row_copy_wait();
+    const double *pS = ph, *pX = ph + nx, *pN = ph + 2 * nx;
+    auto wrap = [&](int i) { return i >= nx ? i - nx : i; };
+    double rr = 0.0, RR = 0.0;
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+        const int ie = wrap(i + 1), iw = (i == 0) ? nx - 1 : i - 1;
+        const double xc = pX[i], xe = pX[ie], xw = pX[iw];
+        const double xn = pN[wrap(i + sh[2])], xne = pN[wrap(ie + sh[2])], xnw = pN[wrap(iw + sh[2])];
+        const double xs = pS[wrap(i + sh[0])], xse = pS[wrap(ie + sh[0])], xsw = pS[wrap(iw + sh[0])];
+        const double Rv = __ldg(M.R + row + i);
+        double fe = c.cx[i] * (xn + xne - xs - xse) + c.bx[i] * (xc + xe) + c.ax[i] * (xe - xc);
+        double fw = c.cx[iw] * (xnw + xn - xsw - xs) + c.bx[iw] * (xw + xc) + c.ax[iw] * (xc - xw);
+        double lphi = fe - fw;
+        if (j < ny - 1) lphi += c.ay[i] * (xn - xc) + c.cy[i] * (xe + xne - xw - xnw) + c.by[i] * (xc + xn);
+        if (j > 0) lphi -= c.ays[i] * (xc - xs) + c.cys[i] * (xse + xe - xsw - xw) + c.bys[i] * (xs + xc);
+        lphi -= c.C[i] * xc;
+        const double rv = lphi - Rv;
+        const typename Pol::res rs = (typename Pol::res)rv;
+        v.r[i] = rs;
+        rr += rv * rv;
+        RR += Rv * Rv;
+        sb[pidx(i)] = stage0_input(M, v, eta, (comp)rs, i);
+    }
+    part[S_A] += (typename Acc<Pol>::type)rr;
+    part[S_B] += (typename Acc<Pol>::type)RR;
+    stage0_finish(M, v, j, ws);
 }
 
 template <class Pol>
-__device__ __forceinline__ double member_eta(const MemberDev<Pol> &M) { return ldcg(M.etap); }
+__device__ void phase_le(const MemberDev<Pol> &M, const MemberCtl &c, const RowView<Pol> &v, int j,
+                         unsigned char *ws, typename Acc<Pol>::type (&part)[NSLOT])
+{
+    typedef typename Pol::comp comp;
+    typedef typename Pol::vec vec;
+    typedef typename Acc<Pol>::type acc_t;
+    const int nx = M.nx, ny = M.ny;
+    const int nd = c.nu + 1;
+    stage3_q(ws, M, M.e, M.e32, M.e_s, j);
+    SW_TRACE(101);
+    const comp *stg = (const comp *)ws;
+    // L e of the row, straight into the row's L e storage
+    stencil_row<comp, typename Pol::coef>(stg, stg + nx, stg + 2 * nx, nx, j, ny, coef_of(v), true, (comp *)v.Le,
+                                          false);
+    SW_TRACE(102);
+    const vec *Lpl[KMAX];
+#pragma unroll
+    for (int l = 0; l < KMAX; ++l) Lpl[l] = v.Lpb + (size_t)phys_slot(c, M.k, l < nd ? l : 0) * v.vstride;
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+        const acc_t la = (acc_t)v.Le[i], rv = (acc_t)v.r[i];
+        part[S_A] += la * la;
+        part[S_B] += rv * la;
+#pragma unroll
+        for (int l = 0; l < KMAX; ++l) {
+            if (l < nd) {
+                const acc_t lp = (acc_t)Lpl[l][i];
+                part[S_C0 + l] += la * lp;
+                part[S_T0 + l] += rv * lp;
+            }
+        }
+    }
+}
+
+template <class Pol>
+__device__ void phase_ub(const MemberDev<Pol> &M, const MemberCtl &c, const RowView<Pol> &v,
+                         typename Pol::comp eta, int j, unsigned char *ws, typename Acc<Pol>::type (&part)[NSLOT])
+{
+    typedef typename Pol::comp comp;
+    typedef typename Pol::vec vec;
+    typedef typename Acc<Pol>::type acc_t;
+    const int nx = M.nx;
+    const size_t row = (size_t)j * nx;
+    const int nd = c.nu + 1;                      // directions before the new one
+    comp *sb = (comp *)(ws + sb_offset<Pol>(nx));
+    // the row of Phi, copied while the direction pointers are set up
+    double *phr = (double *)ws;
+    row_copy_issue(phr, M.phi + row, nx * 8);
+    vec *pn = v.pb + (size_t)phys_slot(c, M.k, nd) * v.vstride;
+    vec *Lpn = v.Lpb + (size_t)phys_slot(c, M.k, nd) * v.vstride;
+    const vec *pl[KMAX], *Lpl[KMAX];
+    comp al[KMAX];
+#pragma unroll
+    for (int l = 0; l < KMAX; ++l) {
+        const size_t off = (size_t)phys_slot(c, M.k, l < nd ? l : 0) * v.vstride;
+        pl[l] = v.pb + off;
+        Lpl[l] = v.Lpb + off;
+        al[l] = l < nd ? (comp)c.alpha[l] : (comp)0;
+    }
+    const float esc = q_scale(M, M.e_s, j);
+    const double beta = c.beta;
+    const comp beta_c = (comp)beta;
+    row_copy_wait();
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+        // p_new = e + sum alpha_l p_l and L p_new = L e + sum alpha_l L p_l
+        comp pv = v.el ? v.el[i] : q_load(M, M.e, M.e32, esc, j, i);
+        comp lw = (comp)v.Le[i];
+        comp lps[KMAX];
+#pragma unroll
+        for (int l = 0; l < KMAX; ++l) {
+            lps[l] = comp(0);
+            if (l < nd) {
+                lps[l] = (comp)Lpl[l][i];
+                pv += al[l] * (comp)pl[l][i];
+                lw += al[l] * lps[l];
+            }
+        }
+        const vec ps = (vec)pv, ls = (vec)lw;
+        pn[i] = ps;
+        Lpn[i] = ls;
+        // the step: Phi += beta p_new, r += beta L p_new
+        M.phi[row + i] = phr[i] + beta * (double)ps;
+        typename Pol::res rs;
+        if constexpr (Pol::kMixed) rs = v.r[i] + beta_c * ls;
+        else rs = v.r[i] + beta * ls;
+        v.r[i] = rs;
+        const acc_t ra = (acc_t)rs, la = (acc_t)ls;
+        part[S_A] += ra * ra;
+        part[S_B] += la * la;
+#pragma unroll
+        for (int l = 0; l < KMAX; ++l)
+            if (l < nd) part[S_C0 + l] += la * (acc_t)lps[l];
+        sb[pidx(i)] = stage0_input(M, v, eta, (comp)rs, i);
+    }
+    SW_TRACE(201);
+    stage0_finish(M, v, j, ws);
+}
+
+// ---------------------------------------------------------------------------
+// state transition after a phase, from the member-wide sums tot[slot].  The
+// scalars (alpha, beta, the Gram update, norms) are computed in the policy's
+// accumulation type: FP64 for the FP64 policy, FP32 for the mixed policies,
+// whose vectors are FP32 anyway; the state keeps them in FP64.
+// ---------------------------------------------------------------------------
+template <class Pol>
+__device__ void advance(const MemberDev<Pol> &M, MemberCtl &c, const typename Acc<Pol>::type *tot, bool writer)
+{
+    typedef typename Acc<Pol>::type sc;
+    const int k = M.k, nd = c.nu + 1;
+    // the mixed policies sum the norms in FP32 (relative error < 1e-6): their
+    // exit test keeps that margin below the tolerance
+    const double tolR = M.tol * c.nR * (Pol::kMixed ? (1.0 - 1e-5) : 1.0);
+    bool done = false;
+    auto to_precond = [&]() { c.stage = 1; c.phase = (M.nstages > 1) ? PH_PREC : PH_LE; };
+    auto finish = [&](int st) { c.status = st; done = true; };
+    switch (c.phase) {
+    case PH_TRUE: {
+        const double rn = sqrt((double)tot[S_A]);
+        if (c.init) {
+            c.init = 0;
+            c.nR = sqrt((double)tot[S_B]);
+            c.r0 = rn;
+            c.rn_true = c.rn_rec = rn;
+            c.nu = -1;
+            if (writer && M.hist) M.hist[0] = c.nR > 0.0 ? rn / c.nR : 0.0;
+            if (c.nR == 0.0) { c.phase = PH_ZERO; break; }
+            if (!isfinite(rn) || !isfinite(c.nR)) { finish(ST_NONFINITE); break; }
+            if (rn <= M.tol * c.nR * (Pol::kMixed ? (1.0 - 1e-5) : 1.0) && M.min_iters <= 0) { finish(ST_OK); break; }
+            to_precond();
+        } else {
+            c.rn_true = rn;
+            if (writer && M.hist) M.hist[c.it] = rn / c.nR;
+            if (!isfinite(rn)) { finish(ST_NONFINITE); break; }
+            if (rn <= tolR && c.it >= M.min_iters) { finish(ST_OK); break; }
+            if (c.it >= M.max_iters) { finish(ST_NOT_CONVERGED); break; }
+            to_precond();
+        }
+        break;
+    }
+    case PH_PREC:
+        c.stage += 1;
+        if (c.stage >= M.nstages) c.phase = PH_LE;
+        break;
+    case PH_LE: {
+        // alpha_l of the text; <Lp_new, Lp_new> and <r, Lp_new> of the
+        // direction Lp_new = Le + sum alpha_l Lp_l, from the Gram matrix
+        sc a[KMAX], lplp = tot[S_A], rlp = tot[S_B];
+        for (int l = 0; l < nd; ++l) a[l] = -tot[S_C0 + l] / (sc)c.G[l][l];
+        for (int l = 0; l < nd; ++l) {
+            sc rowv = (sc)2 * tot[S_C0 + l];
+            for (int m = 0; m < nd; ++m) rowv += a[m] * (sc)c.G[l][m];
+            lplp += a[l] * rowv;
+            rlp += a[l] * tot[S_T0 + l];
+            c.alpha[l] = (double)a[l];
+        }
+        if (!(lplp > sc(0)) || !isfinite(lplp) || !isfinite(rlp)) { finish(ST_BREAKDOWN); break; }
+        c.beta = (double)(-rlp / lplp);
+        c.phase = PH_UB;
+        break;
+    }
+    case PH_UB: {
+        const int ln = nd;                        // logical index of the new direction
+        c.it += 1;
+        const double rn = sqrt((double)tot[S_A]);
+        c.rn_rec = rn;
+        if (writer && M.hist) M.hist[c.it] = rn / c.nR;
+        c.G[ln][ln] = (double)tot[S_B];
+        for (int m = 0; m < ln; ++m) c.G[ln][m] = c.G[m][ln] = (double)tot[S_C0 + m];
+        c.nu = ln;
+        if (c.nu == k) {                          // restart: p_0 <- p_k
+            c.base = phys_slot(c, k, k);
+            c.G[0][0] = c.G[k][k];
+            c.nu = 0;
+        }
+        if (!isfinite(rn)) { finish(ST_NONFINITE); break; }
+        if ((rn <= tolR && c.it >= M.min_iters) || (M.ru_every > 0 && c.it % M.ru_every == 0) ||
+            c.it >= M.max_iters)
+            c.phase = PH_TRUE;
+        else
+            to_precond();
+        break;
+    }
+    case PH_ZERO:
+        c.rn_true = c.rn_rec = 0.0;
+        finish(ST_OK);
+        break;
+    default: break;
+    }
+    if (done) c.phase = PH_DONE;
+}
 
 // ---------------------------------------------------------------------------
 // the persistent GCR kernel
 // ---------------------------------------------------------------------------
 template <class Pol>
-__global__ void __launch_bounds__(MAX_THREADS) k_gcr(EnsembleParams P, int max_nx)
+__global__ void __launch_bounds__(MAX_THREADS) k_gcr(const EnsDesc *__restrict__ D, int max_nx)
 {
+    typedef typename Pol::comp comp;
+    typedef typename Acc<Pol>::type acc_t;
     extern __shared__ __align__(16) unsigned char dsm[];
-    __shared__ int s_off[MAX_MEMBERS + 1];
     __shared__ MemberDev<Pol> s_M;
     __shared__ MemberCtl s_c;
-    __shared__ int s_last;
-    RowSmem<Pol> sm = carve_smem<Pol>(dsm, max_nx);
-    GlobalCtl *G = &P.blk[0]->g;
-    const int n = P.n;
-    const int lane = threadIdx.x & 31;
-
-    for (int step = 0;; ++step) {
-        // enumerate the rows of the active members
-        if (threadIdx.x < 32) {
-            int carry = 0;
-            for (int base = 0; base < n; base += 32) {
-                int m = base + lane, rows = 0;
-                if (m < n) {
-                    SolverBlock *b = P.blk[m];
-                    if (ldcg(&b->ctl.phase) < PH_DONE) rows = mdev<Pol>(b)->ny;
-                }
-                int v = rows;
-#pragma unroll
-                for (int d = 1; d < 32; d <<= 1) {
-                    int o = __shfl_up_sync(0xffffffffu, v, d);
-                    if (lane >= d) v += o;
-                }
-                if (m < n) s_off[m + 1] = carry + v;
-                carry += __shfl_sync(0xffffffffu, v, 31);
-            }
-            if (lane == 0) s_off[0] = 0;
+    __shared__ int s_m, s_ok;
+    __shared__ acc_t s_blk[32];
+    __shared__ acc_t s_tot[NSLOT];
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = D->n;
+        while (hi - lo > 1) {
+            int mid = (lo + hi) >> 1;
+            if (D->cta_begin[mid] <= (int)blockIdx.x) lo = mid; else hi = mid;
         }
-        __syncthreads();
-        const int total = s_off[n];
-        if (total == 0) break;
-        const int per = (total + gridDim.x - 1) / gridDim.x;
-        const int lo = min((int)blockIdx.x * per, total), hi = min(lo + per, total);
-
-        int m = -1, cnt = 0;
-        for (int item = lo; item < hi; ++item) {
-            if (m < 0 || item >= s_off[m + 1]) {
-                if (m >= 0) {
-                    // hand over: count my rows of member m
-                    __syncthreads();
-                    if (threadIdx.x == 0) {
-                        __threadfence();
-                        int old = atomicAdd(&P.blk[m]->ctl.arrive, cnt);
-                        s_last = (old + cnt == s_M.ny);
-                    }
-                    __syncthreads();
-                    if (s_last) { __threadfence(); member_serial<Pol>(P.blk[m], s_M, s_c, sm); }
-                }
-                int mm = (m < 0) ? 0 : m + 1;
-                while (item >= s_off[mm + 1]) ++mm;
-                m = mm;
-                cnt = 0;
-                __syncthreads();
-                copy_in(&s_M, mdev<Pol>(P.blk[m]));
-                copy_in(&s_c, &P.blk[m]->ctl);
-                __syncthreads();
-            }
-            const int j = item - s_off[m];
-            const double eta = member_eta(s_M);
+        s_m = lo;
+    }
+    __syncthreads();
+    const int m = s_m;
+    SolverBlock *B = D->blk[m];
+    const int nb = D->cta_begin[m + 1] - D->cta_begin[m];
+    const int local = (int)blockIdx.x - D->cta_begin[m];
+    copy_in(&s_M, mdev<Pol>(B));
+    copy_in(&s_c, &B->ctl);
+    __syncthreads();
+    const MemberDev<Pol> &M = s_M;
+    const int ny = M.ny, nx = M.nx;
+    unsigned char *ws = dsm;
+    acc_t *scratch = (acc_t *)(ws + red_offset<Pol>(nx));
+    unsigned char *cslot = dsm + work_bytes<Pol>(max_nx);
+    unsigned char *sslot = cslot + (D->cache_const ? const_bytes<Pol>(max_nx) : 0);
+    // this block's rows: j = local + t * nb; the first one may be cached
+    const int j0 = local;
+    const bool single = (j0 + nb >= ny);
+    RowView<Pol> vc;
+    if (j0 < ny) {
+        if (D->cache_const && single) view_const_cache(M, j0, cslot, vc); else view_const_global(M, j0, vc);
+        if (D->cache_state && single) view_state_cache(M, sslot, vc); else view_state_global(M, j0, vc);
+    }
+    __syncthreads();
+    const comp eta = (comp)(*M.etap);
+    GlobalCtl *G = &B->g;
+    acc_t *partg = (acc_t *)M.part;
+    bool ok = true;
+    int par = 0;
+    for (int step = 0; s_c.phase != PH_DONE; ++step) {
+        SW_TRACE(10 + s_c.phase);
+        acc_t part[NSLOT];
+#pragma unroll
+        for (int q = 0; q < NSLOT; ++q) part[q] = acc_t(0);
+        for (int j = j0; j < ny; j += nb) {
+            RowView<Pol> v;
+            if (j == j0) v = vc;
+            else { view_const_global(M, j, v); view_state_global(M, j, v); }
             switch (s_c.phase) {
-            case PH_TRUE: phase_true<Pol>(s_M, s_c, eta, j, sm); break;
-            case PH_BETA: phase_beta<Pol>(s_M, s_c, eta, j, sm); break;
-            case PH_PREC: phase_prec<Pol>(s_M, s_c, eta, j, sm); break;
-            case PH_LE: phase_le<Pol>(s_M, s_c, j, sm); break;
-            case PH_UPD: phase_upd<Pol>(s_M, s_c, j, sm); break;
-            case PH_ZERO: phase_zero<Pol>(s_M, j); break;
+            case PH_TRUE: phase_true<Pol>(M, v, eta, j, ws, part); break;
+            case PH_UB: phase_ub<Pol>(M, s_c, v, eta, j, ws, part); break;
+            case PH_PREC: precond_stage<Pol>(M, v, eta, s_c.stage, j, ws); break;
+            case PH_LE: phase_le<Pol>(M, s_c, v, j, ws, part); break;
+            case PH_ZERO:
+                for (int i = threadIdx.x; i < nx; i += blockDim.x) M.phi[(size_t)j * nx + i] = 0.0;
+                break;
             default: break;
             }
-            ++cnt;
         }
-        if (m >= 0) {
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                __threadfence();
-                int old = atomicAdd(&P.blk[m]->ctl.arrive, cnt);
-                s_last = (old + cnt == s_M.ny);
+        SW_TRACE(30);
+        // block sums of the partials, published slot-major
+        int slot[NSLOT];
+        const int ns = phase_slots(s_c.phase, s_c.nu + 1, slot);
+        acc_t *pbuf = partg + (size_t)par * NSLOT * ny;
+        if (ns > 0) {
+            block_sum_many<NSLOT, acc_t>(part, s_blk, scratch);
+            if (threadIdx.x < ns) pbuf[(size_t)threadIdx.x * ny + local] = s_blk[slot[threadIdx.x]];
+        }
+        __syncthreads();
+        SW_TRACE(31);
+        // member barrier: monotonic arrival counter
+        if (threadIdx.x == 0) {
+            int okb = 1;
+            red_release_add(&G->count, 1ull);
+            const unsigned long long target = (unsigned long long)nb * (unsigned long long)(step + 1);
+            if (ld_acquire(&G->count) < target) {
+                const unsigned long long t0 = gtimer();
+                while (ld_acquire(&G->count) < target) {
+                    if (vload(&G->abort)) { okb = 0; break; }
+                    if (gtimer() - t0 > WAIT_LIMIT_NS) {
+                        if (atomicExch(&G->abort, 1) == 0) G->where = step;
+                        okb = 0;
+                        break;
+                    }
+                    __nanosleep(32);
+                }
             }
-            __syncthreads();
-            if (s_last) { __threadfence(); member_serial<Pol>(P.blk[m], s_M, s_c, sm); }
+            s_ok = okb;
         }
-        if (!grid_barrier(G, step)) return;
+        __syncthreads();
+        if (!s_ok) { ok = false; break; }
+        SW_TRACE(32);
+        // member-wide sums, every block in the same order: warp w adds slots
+        // w, w + nwarps, ... over the member's blocks
+        if (ns > 0) {
+            const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+            for (int q = w; q < ns; q += nw) {
+                const acc_t *src = pbuf + (size_t)q * ny;
+                acc_t t = 0;
+#pragma unroll 8
+                for (int b = lane; b < nb; b += 32) t += __ldcg(src + b);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+                if (lane == 0) s_tot[slot[q]] = t;
+            }
+        }
+        __syncthreads();
+        SW_TRACE(33);
+        if (threadIdx.x == 0) advance<Pol>(M, s_c, s_tot, local == 0);
+        __syncthreads();
+        SW_TRACE(34);
+        par ^= 1;
+    }
+    if (local == 0 && threadIdx.x == 0) {
+        const int *src = (const int *)&s_c;
+        int *dst = (int *)&B->ctl;
+        for (int q = 0; q < (int)(sizeof(MemberCtl) / 4); ++q) dst[q] = src[q];
+    }
+    // per-row norms of the final true residual
+    if (ok && M.rowres && (s_c.status == ST_OK || s_c.status == ST_NOT_CONVERGED)) {
+        for (int j = j0; j < ny; j += nb) {
+            const typename Pol::res *r = (j == j0) ? vc.r : M.r + (size_t)j * nx;
+            double t = 0.0;
+            if (s_c.nR > 0.0)
+                for (int i = threadIdx.x; i < nx; i += blockDim.x) { double x = (double)r[i]; t += x * x; }
+            double tv[1] = {t};
+            block_sum_many<1, double>(tv, (double *)s_blk, (double *)scratch);
+            if (threadIdx.x == 0) M.rowres[j] = sqrt(((double *)s_blk)[0]);
+            __syncthreads();
+        }
     }
 }
 
@@ -468,45 +485,44 @@ __global__ void __launch_bounds__(MAX_THREADS) k_operator(OpArgs<CT> a, const T 
     extern __shared__ __align__(16) unsigned char dsm[];
     T *s3 = (T *)dsm;
     const int nx = a.nx, ny = a.ny, j = blockIdx.x;
-    stage3<T>(s3, nx, ny, j, [&](int jj, int ii) { return x[(size_t)jj * nx + ii]; });
-    for (int i = threadIdx.x; i < nx; i += blockDim.x)
-        y[(size_t)j * nx + i] = stencil<T, CT>(s3, s3 + nx, s3 + 2 * nx, i, nx, j, ny, a.ax, a.cx, a.bx,
-                                                a.ay, a.cy, a.by, a.C, true);
+    const size_t row = (size_t)j * nx, rs = j > 0 ? row - nx : row;
+    const RowCoef<CT> c = {a.ax + row, a.cx + row, a.bx + row, a.ay + row, a.cy + row, a.by + row,
+                           a.ay + rs, a.cy + rs, a.by + rs, a.C + row};
+    for (int r = 0; r < 3; ++r) {
+        int src, sh;
+        ghost_row(j - 1 + r, nx, ny, src, sh);
+        for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+            int ii = i + sh;
+            if (ii >= nx) ii -= nx;
+            s3[r * nx + i] = x[(size_t)src * nx + ii];
+        }
+    }
+    __syncthreads();
+    stencil_row<T, CT>(s3, s3 + nx, s3 + 2 * nx, nx, j, ny, c, true, y + row, false);
 }
 
-// first preconditioner stage from a residual r (type RT)
-template <class Pol, class RT>
-__global__ void __launch_bounds__(MAX_THREADS) k_precond_first(const MemberDev<Pol> *Mp, const RT *r)
+// one preconditioner stage of every row (stage 0 from the residual r)
+template <class Pol>
+__global__ void __launch_bounds__(MAX_THREADS) k_precond(const MemberDev<Pol> *Mp, int mu)
 {
+    typedef typename Pol::comp comp;
     extern __shared__ __align__(16) unsigned char dsm[];
     __shared__ MemberDev<Pol> s_M;
     copy_in(&s_M, Mp);
     __syncthreads();
-    RowSmem<Pol> sm = carve_smem<Pol>(dsm, s_M.nx);
-    const int j = blockIdx.x;
-    const size_t row = (size_t)j * s_M.nx;
-    for (int i = threadIdx.x; i < s_M.nx; i += blockDim.x)
-        sm.sb[i] = stage0_input(s_M, ldcg(s_M.etap), (typename Pol::comp)r[row + i], row + i);
-    stage0_finish(s_M, j, sm);
-}
-
-template <class Pol, class RT>
-__global__ void __launch_bounds__(MAX_THREADS) k_precond_stage(const MemberDev<Pol> *Mp, const RT *r, int mu)
-{
-    extern __shared__ __align__(16) unsigned char dsm[];
-    __shared__ MemberDev<Pol> s_M;
-    copy_in(&s_M, Mp);
-    __syncthreads();
-    RowSmem<Pol> sm = carve_smem<Pol>(dsm, s_M.nx);
     const MemberDev<Pol> &M = s_M;
-    const bool last = (mu == M.nstages - 1);
-    const typename Pol::q16 *ih = (mu & 1) ? M.qa : M.qb;
-    const float *if32 = (mu & 1) ? M.qa32 : M.qb32;
-    const float *is = (mu & 1) ? M.qa_s : M.qb_s;
-    typename Pol::q16 *oh = last ? M.e : ((mu & 1) ? M.qb : M.qa);
-    float *of32 = last ? M.e32 : ((mu & 1) ? M.qb32 : M.qa32);
-    float *os = last ? M.e_s : ((mu & 1) ? M.qb_s : M.qa_s);
-    precond_stage(M, ldcg(M.etap), (int)blockIdx.x, sm, ih, if32, is, r, oh, of32, os);
+    const int j = blockIdx.x;
+    RowView<Pol> v;
+    view_const_global(M, j, v);
+    view_state_global(M, j, v);
+    const comp eta = (comp)(*M.etap);
+    if (mu == 0) {
+        comp *sb = (comp *)(dsm + sb_offset<Pol>(M.nx));
+        for (int i = threadIdx.x; i < M.nx; i += blockDim.x) sb[pidx(i)] = stage0_input(M, v, eta, (comp)v.r[i], i);
+        stage0_finish(M, v, j, dsm);
+    } else {
+        precond_stage<Pol>(M, v, eta, mu, j, dsm);
+    }
 }
 
 // dequantise the preconditioner output e into q (mixed policies)
@@ -528,33 +544,57 @@ __global__ void k_fill(double *p, size_t n, double v)
 // host-side launchers (declared in sw_internal.h)
 // ---------------------------------------------------------------------------
 template <class Pol>
-static cudaError_t launch_gcr_t(const EnsembleParams &P, int max_nx, int threads, int sms, int total_rows,
-                                cudaStream_t s, int *grid_used)
+static size_t smem_t(int max_nx, int k, int cache_const, int cache_state)
 {
-    size_t smem = row_smem_bytes<Pol>(max_nx, threads);
+    return work_bytes<Pol>(max_nx) + (cache_const ? const_bytes<Pol>(max_nx) : 0) +
+           (cache_state ? state_bytes<Pol>(max_nx, k) : 0);
+}
+
+size_t gcr_smem_bytes(int prec, int max_nx, int k, int cache_const, int cache_state)
+{
+    switch (prec) {
+    case 0: return smem_t<PolFP64>(max_nx, k, cache_const, cache_state);
+    case 1: return smem_t<PolF16>(max_nx, k, cache_const, cache_state);
+    default: return smem_t<PolBF16>(max_nx, k, cache_const, cache_state);
+    }
+}
+
+template <class Pol>
+static cudaError_t occupancy_t(int threads, size_t smem, int *blocks_per_sm)
+{
+    if (smem > 227 * 1024 - 8192) { *blocks_per_sm = 0; return cudaSuccess; }
     cudaError_t e = cudaFuncSetAttribute(k_gcr<Pol>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    int nb = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_gcr<Pol>, threads, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_gcr<Pol>, threads, smem);
+}
+
+cudaError_t gcr_occupancy(int prec, int threads, size_t smem, int *blocks_per_sm)
+{
+    switch (prec) {
+    case 0: return occupancy_t<PolFP64>(threads, smem, blocks_per_sm);
+    case 1: return occupancy_t<PolF16>(threads, smem, blocks_per_sm);
+    case 2: return occupancy_t<PolBF16>(threads, smem, blocks_per_sm);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <class Pol>
+static cudaError_t launch_gcr_t(const EnsDesc *Ddev, int grid, int max_nx, int threads, size_t smem, cudaStream_t s)
+{
+    cudaError_t e = cudaFuncSetAttribute(k_gcr<Pol>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    if (nb < 1) return cudaErrorInvalidConfiguration;
-    int grid = nb * sms;
-    if (grid > total_rows) grid = total_rows;
-    if (grid < 1) grid = 1;
-    *grid_used = grid;
-    EnsembleParams Pc = P;
+    const EnsDesc *d = Ddev;
     int mx = max_nx;
-    void *args[] = {(void *)&Pc, (void *)&mx};
+    void *args[] = {(void *)&d, (void *)&mx};
     return cudaLaunchCooperativeKernel((const void *)k_gcr<Pol>, dim3(grid), dim3(threads), args, smem, s);
 }
 
-cudaError_t launch_gcr(int prec, const EnsembleParams &P, int max_nx, int threads, int sms, int total_rows,
-                       cudaStream_t s, int *grid_used)
+cudaError_t launch_gcr(int prec, const EnsDesc *Ddev, int grid, int max_nx, int threads, size_t smem, cudaStream_t s)
 {
     switch (prec) {
-    case 0: return launch_gcr_t<PolFP64>(P, max_nx, threads, sms, total_rows, s, grid_used);
-    case 1: return launch_gcr_t<PolF16>(P, max_nx, threads, sms, total_rows, s, grid_used);
-    case 2: return launch_gcr_t<PolBF16>(P, max_nx, threads, sms, total_rows, s, grid_used);
+    case 0: return launch_gcr_t<PolFP64>(Ddev, grid, max_nx, threads, smem, s);
+    case 1: return launch_gcr_t<PolF16>(Ddev, grid, max_nx, threads, smem, s);
+    case 2: return launch_gcr_t<PolBF16>(Ddev, grid, max_nx, threads, smem, s);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -577,32 +617,41 @@ cudaError_t launch_operator_f32(const OpArgs<float> &a, const float *x, float *y
     return cudaGetLastError();
 }
 
-template <class Pol, class RT>
-static cudaError_t launch_precond_t(const void *Mdev, int nx, int ny, int nstages, const RT *r, float *qout,
-                                    int threads, cudaStream_t s)
+template <class Pol>
+static cudaError_t launch_precond_t(const void *Mdev, int nx, int ny, int nstages, float *qout, int threads,
+                                    cudaStream_t s)
 {
     const MemberDev<Pol> *M = (const MemberDev<Pol> *)Mdev;
-    size_t smem = row_smem_bytes<Pol>(nx, threads);
-    cudaError_t e = cudaFuncSetAttribute(k_precond_first<Pol, RT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    size_t smem = work_bytes<Pol>(nx);
+    cudaError_t e = cudaFuncSetAttribute(k_precond<Pol>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_precond_stage<Pol, RT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_precond_first<Pol, RT><<<ny, threads, smem, s>>>(M, r);
-    for (int mu = 1; mu < nstages; ++mu) k_precond_stage<Pol, RT><<<ny, threads, smem, s>>>(M, r, mu);
-    if (qout) k_unpack_e<Pol><<<ny, threads, 0, s>>>(M, qout);
+    for (int mu = 0; mu < nstages; ++mu) k_precond<Pol><<<ny, threads, smem, s>>>(M, mu);
+    if (qout) k_unpack_e<Pol><<<ny, 128, 0, s>>>(M, qout);
     return cudaGetLastError();
 }
 
-cudaError_t launch_precond(int prec, const void *Mdev, int nx, int ny, int nstages, const void *r, void *qout,
-                           int threads, cudaStream_t s)
+cudaError_t launch_precond(int prec, const void *Mdev, int nx, int ny, int nstages, void *qout, int threads,
+                           cudaStream_t s)
 {
     switch (prec) {
-    case 0: return launch_precond_t<PolFP64, double>(Mdev, nx, ny, nstages, (const double *)r, nullptr, threads, s);
-    case 1: return launch_precond_t<PolF16, float>(Mdev, nx, ny, nstages, (const float *)r, (float *)qout, threads, s);
-    case 2: return launch_precond_t<PolBF16, float>(Mdev, nx, ny, nstages, (const float *)r, (float *)qout, threads, s);
+    case 0: return launch_precond_t<PolFP64>(Mdev, nx, ny, nstages, nullptr, threads, s);
+    case 1: return launch_precond_t<PolF16>(Mdev, nx, ny, nstages, (float *)qout, threads, s);
+    case 2: return launch_precond_t<PolBF16>(Mdev, nx, ny, nstages, (float *)qout, threads, s);
     default: return cudaErrorInvalidValue;
     }
 }
+
+#ifdef SW_PHASE_TRACE
+// configure the device timeline (traced builds only): buffer of 2*cap words
+extern "C" void sw_trace_configure(unsigned long long *buf, int cap, int block)
+{
+    int z = 0;
+    cudaMemcpyToSymbol(g_trace_buf, &buf, sizeof(buf));
+    cudaMemcpyToSymbol(g_trace_n, &z, sizeof(z));
+    cudaMemcpyToSymbol(g_trace_cap, &cap, sizeof(cap));
+    cudaMemcpyToSymbol(g_trace_blk, &block, sizeof(block));
+}
+#endif
 
 cudaError_t launch_fill(double *p, size_t n, double v, cudaStream_t s)
 {
