@@ -169,6 +169,41 @@ sw_status sw_ensemble_solve(int n, const sw_grid *grids, const sw_solve_opts *o,
                             const double *const *R, double *const *phi,
                             sw_solve_stats *stats, void *stream);
 
+/* Size of the fixed device scratch used by sw_gcr_solve_noalloc. */
+#define SW_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/* sw_gcr_solve without any allocation.  The paper has no counterpart: this
+ * entry point exists for callers that may not allocate device memory in the
+ * middle of their time step.  Examples are a model that has already handed
+ * all of its device memory to its own pool, and a pipeline that must not
+ * stall: cudaMalloc and cudaFree can synchronise the whole device.
+ *
+ * Arguments, results, statuses and the solution are those of sw_gcr_solve with
+ * the same grid and options.  The difference is where the solver's work
+ * vectors live.  They are not in the grid's workspace, and nothing is
+ * allocated for them.  They go in one fixed array of SW_NOALLOC_SCRATCH_BYTES
+ * per device, built into the library and shared by every grid on that device.
+ * The call makes no device or pinned-host allocation of any kind.  On a
+ * failing call, the error message text may use the host heap.
+ *  - Size limit: sw_grid_workspace_bytes(g, o) must not exceed
+ *    SW_NOALLOC_SCRATCH_BYTES.  A larger grid is rejected with
+ *    SW_ERR_INVALID_ARG before anything runs.  For example, 512 x 256 with
+ *    k <= 4 fits in FP64 and in the mixed precisions.
+ *  - Nothing has to start at zero.  The solver writes every scratch value
+ *    before it reads it, and each call resets the grid's own barrier
+ *    counters.
+ *  - Overlapping calls race.  Two calls on one device that can run at the
+ *    same time share the scratch and corrupt each other's results: for
+ *    example, calls from two host threads or calls on two streams.  Issue
+ *    them one after another.  Each call waits for its own solve on `stream`
+ *    before it returns.
+ *  - The first call on each device looks up the scratch's device address.
+ *    That is a one-time setup step and may load the library's device code.
+ *    Make this first call, with that device current, before any stream
+ *    capture begins. */
+sw_status sw_gcr_solve_noalloc(sw_grid g, const sw_solve_opts *o, const double *R, double *phi,
+                               sw_solve_stats *stats, void *stream);
+
 /* Message describing the last error on the calling host thread. */
 const char *sw_last_error(void);
 

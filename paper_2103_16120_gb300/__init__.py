@@ -16,7 +16,7 @@ from ._lib import (  # noqa: F401
     SW_OK, SW_ERR_INVALID_ARG, SW_ERR_CUDA, SW_ERR_OOM, SW_ERR_NOT_CONVERGED, SW_ERR_BREAKDOWN,
     SW_ERR_NONFINITE, SW_ERR_TIMEOUT, SW_ERR_INTERNAL,
     SW_PREC_FP64, SW_PREC_MIXED_FP16, SW_PREC_MIXED_BF16, SW_PREC_FP32,
-    SW_PC_NONE, SW_PC_DIAG, SW_PC_DIAG_RICHARDSON, SW_PC_SI_RICHARDSON,
+    SW_PC_NONE, SW_PC_DIAG, SW_PC_DIAG_RICHARDSON, SW_PC_SI_RICHARDSON, SW_NOALLOC_SCRATCH_BYTES,
 )
 
 COEFF_KEYS = ("A11", "A12", "A21", "A22", "B1", "B2", "C")
@@ -157,6 +157,18 @@ def sw_gcr_solve(g: Grid, opts: SolveOpts, R, phi, stream=None) -> SolveStats:
     _check(load().sw_gcr_solve(g.handle, C.byref(opts), _ptr(R, torch.float64, shp),
                                _ptr(phi, torch.float64, shp), C.byref(st), _stream(stream)),
            "sw_gcr_solve", SOLVE_OUTCOMES)
+    return st
+
+
+def sw_gcr_solve_noalloc(g: Grid, opts: SolveOpts, R, phi, stream=None) -> SolveStats:
+    """sw_gcr_solve with the work vectors in the library's fixed device scratch
+    (no allocation; grids up to SW_NOALLOC_SCRATCH_BYTES of workspace)."""
+    import torch
+    shp = (g.ny, g.nx)
+    st = SolveStats()
+    _check(load().sw_gcr_solve_noalloc(g.handle, C.byref(opts), _ptr(R, torch.float64, shp),
+                                       _ptr(phi, torch.float64, shp), C.byref(st), _stream(stream)),
+           "sw_gcr_solve_noalloc", SOLVE_OUTCOMES)
     return st
 
 

@@ -23,8 +23,10 @@ SW_PC_NONE, SW_PC_DIAG, SW_PC_DIAG_RICHARDSON, SW_PC_SI_RICHARDSON = range(4)
 EXPORTS = (
     "sw_solve_opts_default", "sw_grid_create", "sw_grid_destroy", "sw_grid_workspace_bytes",
     "sw_grid_attach_workspace", "sw_elliptic_set_coeffs", "sw_grid_set_eta", "sw_grid_get_eta",
-    "sw_operator_apply", "sw_precond_apply", "sw_gcr_solve", "sw_ensemble_solve", "sw_last_error",
+    "sw_operator_apply", "sw_precond_apply", "sw_gcr_solve", "sw_ensemble_solve", "sw_gcr_solve_noalloc",
+    "sw_last_error",
 )
+SW_NOALLOC_SCRATCH_BYTES = 16 << 20
 
 
 class SolveOpts(C.Structure):
@@ -69,6 +71,7 @@ def load() -> C.CDLL:
     lib.sw_operator_apply.argtypes = [vp, i, vp, vp, vp]
     lib.sw_precond_apply.argtypes = [vp, C.POINTER(SolveOpts), vp, vp, vp]
     lib.sw_gcr_solve.argtypes = [vp, C.POINTER(SolveOpts), vp, vp, C.POINTER(SolveStats), vp]
+    lib.sw_gcr_solve_noalloc.argtypes = [vp, C.POINTER(SolveOpts), vp, vp, C.POINTER(SolveStats), vp]
     lib.sw_ensemble_solve.argtypes = [i, C.POINTER(vp), C.POINTER(SolveOpts), C.POINTER(vp),
                                       C.POINTER(vp), C.POINTER(SolveStats), vp]
     lib.sw_last_error.argtypes = []

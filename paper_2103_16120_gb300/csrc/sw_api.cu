@@ -1,6 +1,7 @@
 // sw_api.cu -- the C ABI declared in include/sw_elliptic.h: grid handles,
 // coefficient storage, workspace, argument checks and kernel launches.
 #include <string>
+#include <cstdio>
 #include <cstring>
 #include <cmath>
 #include <new>
@@ -570,4 +571,120 @@ extern "C" sw_status sw_ensemble_solve(int n, const sw_grid *grids, const sw_sol
 {
     if (!grids || !R || !phi) return fail(SW_ERR_INVALID_ARG, "sw_ensemble_solve: NULL argument");
     return solve_members(n, grids, o, R, phi, stats, (cudaStream_t)stream);
+}
+
+// ---------------------------------------------------------------------------
+// the solve of one grid with its work vectors in the fixed scratch: the same
+// kernel and launch shape as sw_gcr_solve, with no allocation
+// ---------------------------------------------------------------------------
+template <class Pol>
+static void fill_member_noalloc(const sw_grid_s *g, void *scratch, const sw_solve_opts *o, const double *R,
+                                double *phi, void *out)
+{
+    sw_grid_s view = *g;          // a copy of the handle that points at the scratch
+    view.ws = scratch;
+    MemberDev<Pol> M;
+    fill_member<Pol>(&view, o, R, phi, M);
+    std::memcpy(out, &M, sizeof(M));
+}
+
+extern "C" sw_status sw_gcr_solve_noalloc(sw_grid g, const sw_solve_opts *o, const double *R, double *phi,
+                                          sw_solve_stats *stats, void *stream)
+{
+    if (!g || !R || !phi) return fail(SW_ERR_INVALID_ARG, "sw_gcr_solve_noalloc: NULL argument");
+    sw_status st = check_opts(o, true);
+    if (st) return st;
+    if (!g->has_coeffs) return fail(SW_ERR_INVALID_ARG, "sw_gcr_solve_noalloc: coefficients not set");
+    int dev = -1;
+    CK(cudaGetDevice(&dev));
+    if (g->device != dev) return fail(SW_ERR_INVALID_ARG, "sw_gcr_solve_noalloc: the grid belongs to another device");
+    const size_t need = ws_layout(g, o->prec, o->k).total;
+    if (need > SW_NOALLOC_SCRATCH_BYTES) {
+        char msg[200];
+        std::snprintf(msg, sizeof(msg),
+                      "sw_gcr_solve_noalloc: this grid and these options need %zu bytes of scratch, more than the "
+                      "fixed %u (use sw_gcr_solve)", need, (unsigned)SW_NOALLOC_SCRATCH_BYTES);
+        return fail(SW_ERR_INVALID_ARG, msg);
+    }
+    void *scratch = nullptr;
+    size_t cap = 0;
+    CK(noalloc_scratch(&scratch, &cap));
+    cudaStream_t s = (cudaStream_t)stream;
+    if (o->eta > 0.0 && o->eta != g->eta_explicit) {
+        g->eta_explicit = o->eta;
+        if ((st = refactor(g, s))) return st;
+    }
+    alignas(16) unsigned char hbuf[sizeof(SolverBlock::dev)];
+    if (o->prec == SW_PREC_FP64) fill_member_noalloc<PolFP64>(g, scratch, o, R, phi, hbuf);
+    else if (o->prec == SW_PREC_MIXED_FP16) fill_member_noalloc<PolF16>(g, scratch, o, R, phi, hbuf);
+    else fill_member_noalloc<PolBF16>(g, scratch, o, R, phi, hbuf);
+    CK(cudaMemcpyAsync(g->blk->dev, hbuf, member_dev_bytes(o->prec), cudaMemcpyHostToDevice, s));
+    MemberCtl c;
+    std::memset(&c, 0, sizeof(c));
+    c.phase = PH_TRUE;
+    c.init = 1;
+    c.nu = -1;
+    *g->h_ctl = c;
+    CK(cudaMemcpyAsync(&g->blk->ctl, g->h_ctl, sizeof(MemberCtl), cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(&g->blk->g, 0, sizeof(GlobalCtl), s));
+    if (o->res_history) CK(launch_fill(o->res_history, (size_t)o->max_iters + 1, NAN, s));
+
+    // launch shape of a one-member solve: a block per row when they can all
+    // be resident (with as much of the row cached as fits), else as many
+    // blocks as can be resident, each cycling over rows
+    const int threads = row_threads(g->nx, o->threads_per_row);
+    int grid = 0, cc = 0, cs = 0;
+    size_t smem = 0;
+    const int levels[3][2] = {{1, 1}, {1, 0}, {0, 0}};
+    for (int lv = 0; lv < 3 && !grid; ++lv) {
+        const size_t sm_l = gcr_smem_bytes(o->prec, g->nx, o->k, levels[lv][0], levels[lv][1]);
+        int bps = 0;
+        CK(gcr_occupancy(o->prec, threads, sm_l, &bps));
+        if (bps > 0 && g->ny <= bps * g->sms) {
+            grid = g->ny; cc = levels[lv][0]; cs = levels[lv][1]; smem = sm_l;
+        }
+    }
+    if (!grid) {
+        smem = gcr_smem_bytes(o->prec, g->nx, o->k, 0, 0);
+        int bps = 0;
+        CK(gcr_occupancy(o->prec, threads, smem, &bps));
+        if (bps < 1) return fail(SW_ERR_INVALID_ARG, "sw_gcr_solve_noalloc: grid rows too long for the solver kernel");
+        grid = std::min(bps * g->sms, g->ny);
+    }
+    EnsDesc &D = *g->h_desc;
+    D.n = 1;
+    D.grid = grid;
+    D.cache_const = cc;
+    D.cache_state = cs;
+    D.cta_begin[0] = 0;
+    D.cta_begin[1] = grid;
+    D.blk[0] = g->blk;
+    CK(cudaMemcpyAsync(g->desc, &D, sizeof(EnsDesc), cudaMemcpyHostToDevice, s));
+    CK(launch_gcr(o->prec, g->desc, grid, g->nx, threads, smem, s));
+    CK(cudaMemcpyAsync(g->h_ctl, &g->blk->ctl, sizeof(MemberCtl) + sizeof(GlobalCtl), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(g->h_eta, g->eta, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+
+    const MemberCtl &r = *g->h_ctl;
+    const bool timeout = g->h_g->abort != 0;
+    const int mst = timeout ? SW_ERR_TIMEOUT : (r.phase == PH_DONE ? r.status : SW_ERR_INTERNAL);
+    if (stats) {
+        std::memset(stats, 0, sizeof(*stats));
+        stats->iterations = r.it;
+        stats->status = mst;
+        stats->converged = (mst == SW_OK);
+        stats->r0_norm = r.r0;
+        stats->R_norm = r.nR;
+        stats->true_rel_residual = r.nR > 0 ? r.rn_true / r.nR : 0.0;
+        stats->recursive_rel_residual = r.nR > 0 ? r.rn_rec / r.nR : 0.0;
+        stats->eta = *g->h_eta;
+    }
+    switch (mst) {
+    case SW_OK: return SW_OK;
+    case SW_ERR_TIMEOUT: return fail(SW_ERR_TIMEOUT, "a device-side barrier wait ran out");
+    case SW_ERR_NOT_CONVERGED: return fail(SW_ERR_NOT_CONVERGED, "max_iters reached before the tolerance");
+    case SW_ERR_BREAKDOWN: return fail(SW_ERR_BREAKDOWN, "GCR breakdown: <L p, L p> not positive");
+    case SW_ERR_NONFINITE: return fail(SW_ERR_NONFINITE, "non-finite residual norm");
+    default: return fail(SW_ERR_INTERNAL, "solver ended in an unexpected state");
+    }
 }

@@ -1,5 +1,5 @@
 // sw_internal.h -- host-side interfaces between the C ABI (sw_api.cu) and the
-// kernel translation units (sw_solver.cu, sw_setup.cu).
+// kernel translation units (sw_solver.cu, sw_setup.cu, sw_static.cu).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -43,5 +43,7 @@ cudaError_t launch_precond(int prec, const void *Mdev, int nx, int ny, int nstag
                            cudaStream_t s);
 cudaError_t launch_fill(double *p, size_t n, double v, cudaStream_t s);
 size_t member_dev_bytes(int prec);
+// the fixed scratch of sw_gcr_solve_noalloc on the current device (sw_static.cu)
+cudaError_t noalloc_scratch(void **ptr, size_t *bytes);
 
 } // namespace sw

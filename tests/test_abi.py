@@ -48,13 +48,15 @@ def test_struct_layout_matches_c(tmp_path):
              'printf("%zu %zu\\n", sizeof(sw_solve_opts), sizeof(sw_solve_stats));']
     lines += [f'printf("%zu\\n", offsetof(sw_solve_opts, {f}));' for f in fields_o]
     lines += [f'printf("%zu\\n", offsetof(sw_solve_stats, {f}));' for f in fields_s]
-    lines += ["return 0;}"]
+    lines += ['printf("%u\\n", (unsigned)SW_NOALLOC_SCRATCH_BYTES);', "return 0;}"]
     prog.write_text("\n".join(lines))
     exe = tmp_path / "layout"
     subprocess.run(["gcc", str(prog), "-o", str(exe)], check=True)
     vals = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
     assert vals[0] == C.sizeof(SolveOpts) and vals[1] == C.sizeof(SolveStats)
-    offs = vals[2:]
+    from paper_2103_16120_gb300._lib import SW_NOALLOC_SCRATCH_BYTES
+    assert vals[-1] == SW_NOALLOC_SCRATCH_BYTES
+    offs = vals[2:-1]
     assert offs[: len(fields_o)] == [getattr(SolveOpts, f).offset for f in fields_o]
     assert offs[len(fields_o):] == [getattr(SolveStats, f).offset for f in fields_s]
 
@@ -73,6 +75,7 @@ def test_defaults_and_argument_checks_without_gpu(lib):
     assert lib.sw_grid_create(8192, 4, 1.0, C.byref(h)) == SW_ERR_INVALID_ARG
     assert lib.sw_gcr_solve(None, C.byref(o), None, None, None, None) == SW_ERR_INVALID_ARG
     assert lib.sw_ensemble_solve(1, None, C.byref(o), None, None, None, None) == SW_ERR_INVALID_ARG
+    assert lib.sw_gcr_solve_noalloc(None, C.byref(o), None, None, None, None) == SW_ERR_INVALID_ARG
 
 
 def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
