@@ -479,7 +479,7 @@ static sw_status solve_members(int n, const sw_grid *grids, const sw_solve_opts 
     for (int lv = 0; lv < 3 && !grid; ++lv) {
         const size_t sm_l = gcr_smem_bytes(o->prec, max_nx, o->k, levels[lv][0], levels[lv][1]);
         int bps = 0;
-        CK(gcr_occupancy(o->prec, threads, sm_l, &bps));
+        CK(gcr_occupancy(o->prec, o->k, threads, sm_l, &bps));
         if (bps > 0 && rows_total <= (long)bps * sms) {
             for (int m = 0; m < n; ++m) nb[m] = grids[m]->ny;
             grid = (int)rows_total; cc = levels[lv][0]; cs = levels[lv][1]; smem = sm_l;
@@ -489,7 +489,7 @@ static sw_status solve_members(int n, const sw_grid *grids, const sw_solve_opts 
         // several rows per block: spread the co-resident blocks over the members
         smem = gcr_smem_bytes(o->prec, max_nx, o->k, 0, 0);
         int bps = 0;
-        CK(gcr_occupancy(o->prec, threads, smem, &bps));
+        CK(gcr_occupancy(o->prec, o->k, threads, smem, &bps));
         if (bps < 1) return fail(SW_ERR_INVALID_ARG, "grid rows too long for the solver kernel");
         const int cap = bps * sms;
         if (n > cap) return fail(SW_ERR_INVALID_ARG, "too many members for one launch on this device");
@@ -520,7 +520,7 @@ static sw_status solve_members(int n, const sw_grid *grids, const sw_solve_opts 
         D.blk[m] = grids[m]->blk;
     }
     CK(cudaMemcpyAsync(lead->desc, &D, sizeof(EnsDesc), cudaMemcpyHostToDevice, s));
-    CK(launch_gcr(o->prec, lead->desc, grid, max_nx, threads, smem, s));
+    CK(launch_gcr(o->prec, o->k, lead->desc, grid, max_nx, threads, smem, s));
     for (int m = 0; m < n; ++m) {
         sw_grid g = grids[m];
         CK(cudaMemcpyAsync(g->h_ctl, &g->blk->ctl, sizeof(MemberCtl) + sizeof(GlobalCtl), cudaMemcpyDeviceToHost, s));
@@ -639,7 +639,7 @@ extern "C" sw_status sw_gcr_solve_noalloc(sw_grid g, const sw_solve_opts *o, con
     for (int lv = 0; lv < 3 && !grid; ++lv) {
         const size_t sm_l = gcr_smem_bytes(o->prec, g->nx, o->k, levels[lv][0], levels[lv][1]);
         int bps = 0;
-        CK(gcr_occupancy(o->prec, threads, sm_l, &bps));
+        CK(gcr_occupancy(o->prec, o->k, threads, sm_l, &bps));
         if (bps > 0 && g->ny <= bps * g->sms) {
             grid = g->ny; cc = levels[lv][0]; cs = levels[lv][1]; smem = sm_l;
         }
@@ -647,7 +647,7 @@ extern "C" sw_status sw_gcr_solve_noalloc(sw_grid g, const sw_solve_opts *o, con
     if (!grid) {
         smem = gcr_smem_bytes(o->prec, g->nx, o->k, 0, 0);
         int bps = 0;
-        CK(gcr_occupancy(o->prec, threads, smem, &bps));
+        CK(gcr_occupancy(o->prec, o->k, threads, smem, &bps));
         if (bps < 1) return fail(SW_ERR_INVALID_ARG, "sw_gcr_solve_noalloc: grid rows too long for the solver kernel");
         grid = std::min(bps * g->sms, g->ny);
     }
@@ -660,7 +660,7 @@ extern "C" sw_status sw_gcr_solve_noalloc(sw_grid g, const sw_solve_opts *o, con
     D.cta_begin[1] = grid;
     D.blk[0] = g->blk;
     CK(cudaMemcpyAsync(g->desc, &D, sizeof(EnsDesc), cudaMemcpyHostToDevice, s));
-    CK(launch_gcr(o->prec, g->desc, grid, g->nx, threads, smem, s));
+    CK(launch_gcr(o->prec, o->k, g->desc, grid, g->nx, threads, smem, s));
     CK(cudaMemcpyAsync(g->h_ctl, &g->blk->ctl, sizeof(MemberCtl) + sizeof(GlobalCtl), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(g->h_eta, g->eta, sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));

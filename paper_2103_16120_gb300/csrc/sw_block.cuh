@@ -128,15 +128,13 @@ __device__ __forceinline__ void block_affine_excl(T &a, T &b, T *sm)
 // inverse pivots invD; with zz = z / (gam + w.z) the Sherman-Morrison step is
 // x = y - zz (gam y_0 + ec y_{n-1}) (no correction when zz is null).  FP: the
 // factor rows are padded too.  Every thread owns a contiguous chunk of at most
-// RM values held in registers (the row has at most RM * blockDim.x values),
-// so all loads are issued before the recurrences run.
+// RM values held in registers (n <= RM * blockDim.x), so all loads are issued
+// before the recurrences run; trisolve_block picks the smallest RM that fits.
 constexpr int TRI_RM = 16;
 
-template <class T, class F, bool FP>
-__device__ __noinline__ void trisolve_block(T *sb, int n, const F *lf, const F *invD, const F *zz, T gam, T ec,
-                                            T *sm)
+template <int RM, class T, class F, bool FP>
+__device__ __noinline__ void trisolve_rm(T *sb, int n, const F *lf, const F *invD, const F *zz, T gam, T ec, T *sm)
 {
-    constexpr int RM = TRI_RM;
     const int m = (n + blockDim.x - 1) / blockDim.x;
     const int c0 = min((int)threadIdx.x * m, n), c1 = min(c0 + m, n);
     T x[RM], l[RM], d[RM], z[RM];
@@ -189,6 +187,17 @@ __device__ __noinline__ void trisolve_block(T *sb, int n, const F *lf, const F *
     for (int t = 0; t < RM; ++t)
         if (c0 + t < c1) sb[pidx(c0 + t)] = x[t] - z[t] * s;
     __syncthreads();
+}
+
+template <class T, class F, bool FP>
+__device__ __forceinline__ void trisolve_block(T *sb, int n, const F *lf, const F *invD, const F *zz, T gam, T ec,
+                                               T *sm)
+{
+    const int m = (n + blockDim.x - 1) / blockDim.x;
+    if (m <= 2) trisolve_rm<2, T, F, FP>(sb, n, lf, invD, zz, gam, ec, sm);
+    else if (m <= 4) trisolve_rm<4, T, F, FP>(sb, n, lf, invD, zz, gam, ec, sm);
+    else if (m <= 8) trisolve_rm<8, T, F, FP>(sb, n, lf, invD, zz, gam, ec, sm);
+    else trisolve_rm<16, T, F, FP>(sb, n, lf, invD, zz, gam, ec, sm);
 }
 
 // ---------------------------------------------------------------------------

@@ -171,31 +171,51 @@ __device__ __forceinline__ void ghost_row(int jj, int nx, int ny, int &src, int 
 // ---------------------------------------------------------------------------
 // stencils
 // ---------------------------------------------------------------------------
+// elements per thread whose loads a row loop issues together: enough loads in
+// flight to cover the memory latency when the row data are not cached, few
+// enough registers for two resident blocks
+template <class T>
+__host__ __device__ constexpr int batch_of() { return sizeof(T) == 8 ? 2 : 4; }
+
 // y_i = (L x)_i (full) or (P^M x)_i for the whole row from the staged rows
-// S (j-1), X (j), N (j+1); y[pidx(i)] when ypad, else y[i]
+// S (j-1), X (j), N (j+1); y[pidx(i)] when ypad, else y[i].  The coefficients
+// of a batch of elements are loaded before any result is stored.
 template <class T, class CT>
 __device__ __noinline__ void stencil_row(const T *S, const T *X, const T *N, int nx, int j, int ny,
                                          const RowCoef<CT> c, bool full, T *y, bool ypad)
 {
-    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-        const int ie = (i + 1 == nx) ? 0 : i + 1, iw = (i == 0) ? nx - 1 : i - 1;
-        const T xc = X[i], xe = X[ie], xw = X[iw];
-        const T xn = N[i], xne = N[ie], xnw = N[iw];
-        const T xs = S[i], xse = S[ie], xsw = S[iw];
-        const T cx = (T)c.cx[i], cxw = (T)c.cx[iw], bx = (T)c.bx[i], bxw = (T)c.bx[iw];
-        const T ax = full ? (T)c.ax[i] : T(0), axw = full ? (T)c.ax[iw] : T(0);
-        const T ay = (T)c.ay[i], cy = (T)c.cy[i], by = (T)c.by[i];
-        const T ays = (T)c.ays[i], cys = (T)c.cys[i], bys = (T)c.bys[i];
-        const T cc = full ? (T)c.C[i] : T(0);
-        // zonal fluxes through the east (i+1/2) and west (i-1/2) faces
-        T fe = cx * (xn + xne - xs - xse) + bx * (xc + xe) + ax * (xe - xc);
-        T fw = cxw * (xnw + xn - xsw - xs) + bxw * (xw + xc) + axw * (xc - xw);
-        T v = fe - fw;
-        // meridional fluxes through the north (j+1/2) and south (j-1/2)
-        // faces; zero through the pole faces
-        if (j < ny - 1) v += ay * (xn - xc) + cy * (xe + xne - xw - xnw) + by * (xc + xn);
-        if (j > 0) v -= ays * (xc - xs) + cys * (xse + xe - xsw - xw) + bys * (xs + xc);
-        y[ypad ? pidx(i) : i] = v - cc * xc;
+    constexpr int U = batch_of<T>();
+    const int nt = blockDim.x;
+    const bool has_n = j < ny - 1, has_s = j > 0;
+    for (int i0 = threadIdx.x; i0 < nx; i0 += U * nt) {
+        CT cx[U], cxw[U], bx[U], bxw[U], ax[U], axw[U], ay[U], cy[U], by[U], ays[U], cys[U], bys[U], cc[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = min(i0 + u * nt, nx - 1), iw = (i == 0) ? nx - 1 : i - 1;
+            cx[u] = c.cx[i]; cxw[u] = c.cx[iw]; bx[u] = c.bx[i]; bxw[u] = c.bx[iw];
+            ax[u] = full ? c.ax[i] : CT(0); axw[u] = full ? c.ax[iw] : CT(0);
+            ay[u] = has_n ? c.ay[i] : CT(0); cy[u] = has_n ? c.cy[i] : CT(0); by[u] = has_n ? c.by[i] : CT(0);
+            ays[u] = has_s ? c.ays[i] : CT(0); cys[u] = has_s ? c.cys[i] : CT(0); bys[u] = has_s ? c.bys[i] : CT(0);
+            cc[u] = full ? c.C[i] : CT(0);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = i0 + u * nt;
+            if (i >= nx) break;
+            const int ie = (i + 1 == nx) ? 0 : i + 1, iw = (i == 0) ? nx - 1 : i - 1;
+            const T xc = X[i], xe = X[ie], xw = X[iw];
+            const T xn = N[i], xne = N[ie], xnw = N[iw];
+            const T xs = S[i], xse = S[ie], xsw = S[iw];
+            // zonal fluxes through the east (i+1/2) and west (i-1/2) faces
+            T fe = (T)cx[u] * (xn + xne - xs - xse) + (T)bx[u] * (xc + xe) + (T)ax[u] * (xe - xc);
+            T fw = (T)cxw[u] * (xnw + xn - xsw - xs) + (T)bxw[u] * (xw + xc) + (T)axw[u] * (xc - xw);
+            T v = fe - fw;
+            // meridional fluxes through the north (j+1/2) and south (j-1/2)
+            // faces; zero through the pole faces
+            if (has_n) v += (T)ay[u] * (xn - xc) + (T)cy[u] * (xe + xne - xw - xnw) + (T)by[u] * (xc + xn);
+            if (has_s) v -= (T)ays[u] * (xc - xs) + (T)cys[u] * (xse + xe - xsw - xw) + (T)bys[u] * (xs + xc);
+            y[ypad ? pidx(i) : i] = v - (T)cc[u] * xc;
+        }
     }
     __syncthreads();
 }
@@ -393,9 +413,22 @@ __device__ void precond_stage(const MemberDev<Pol> &M, const RowView<Pol> &v, ty
     const comp *S = stg, *X = stg + nx, *N = stg + 2 * nx;
     const bool opt3 = (M.pc == 3);
     stencil_row<comp, typename Pol::coef>(S, X, N, nx, j, ny, coef_of(v), !opt3, sb, true);
-    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-        const comp s = sb[pidx(i)], rv = (comp)v.r[i], xv = X[i];
-        sb[pidx(i)] = opt3 ? xv + eta * (s - rv) : xv + (comp)M.omega * (rv - s) / (comp)v.diag[i];
+    constexpr int U = batch_of<comp>();
+    for (int i0 = threadIdx.x; i0 < nx; i0 += U * blockDim.x) {
+        comp rv[U], dg[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = min(i0 + u * (int)blockDim.x, nx - 1);
+            rv[u] = (comp)v.r[i];
+            dg[u] = opt3 ? comp(1) : (comp)v.diag[i];
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = i0 + u * blockDim.x;
+            if (i >= nx) break;
+            const comp s = sb[pidx(i)], xv = X[i];
+            sb[pidx(i)] = opt3 ? xv + eta * (s - rv[u]) : xv + (comp)M.omega * (rv[u] - s) / dg[u];
+        }
     }
     __syncthreads();
     SW_TRACE(302);

@@ -88,9 +88,9 @@ __device__ __forceinline__ int phase_slots(int phase, int nd, int *slot)
 // phases on one row j (one block).  Each thread adds its share of the phase's
 // inner products to part[slot]; the caller sums them over the block.
 // ---------------------------------------------------------------------------
-template <class Pol>
+template <class Pol, int NP>
 __device__ void phase_true(const MemberDev<Pol> &M, const RowView<Pol> &v, typename Pol::comp eta, int j,
-                           unsigned char *ws, typename Acc<Pol>::type (&part)[NSLOT])
+                           unsigned char *ws, typename Acc<Pol>::type (&part)[NP])
 {
     typedef typename Pol::comp comp;
     const int nx = M.nx, ny = M.ny;
@@ -116,34 +116,50 @@ __device__ void phase_true(const MemberDev<Pol> &M, const RowView<Pol> &v, typen
     row_copy_wait();
     const double *pS = ph, *pX = ph + nx, *pN = ph + 2 * nx;
     auto wrap = [&](int i) { return i >= nx ? i - nx : i; };
+    const bool has_n = j < ny - 1, has_s = j > 0;
     double rr = 0.0, RR = 0.0;
-    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-        const int ie = wrap(i + 1), iw = (i == 0) ? nx - 1 : i - 1;
-        const double xc = pX[i], xe = pX[ie], xw = pX[iw];
-        const double xn = pN[wrap(i + sh[2])], xne = pN[wrap(ie + sh[2])], xnw = pN[wrap(iw + sh[2])];
-        const double xs = pS[wrap(i + sh[0])], xse = pS[wrap(ie + sh[0])], xsw = pS[wrap(iw + sh[0])];
-        const double Rv = __ldg(M.R + row + i);
-        double fe = c.cx[i] * (xn + xne - xs - xse) + c.bx[i] * (xc + xe) + c.ax[i] * (xe - xc);
-        double fw = c.cx[iw] * (xnw + xn - xsw - xs) + c.bx[iw] * (xw + xc) + c.ax[iw] * (xc - xw);
-        double lphi = fe - fw;
-        if (j < ny - 1) lphi += c.ay[i] * (xn - xc) + c.cy[i] * (xe + xne - xw - xnw) + c.by[i] * (xc + xn);
-        if (j > 0) lphi -= c.ays[i] * (xc - xs) + c.cys[i] * (xse + xe - xsw - xw) + c.bys[i] * (xs + xc);
-        lphi -= c.C[i] * xc;
-        const double rv = lphi - Rv;
-        const typename Pol::res rs = (typename Pol::res)rv;
-        v.r[i] = rs;
-        rr += rv * rv;
-        RR += Rv * Rv;
-        sb[pidx(i)] = stage0_input(M, v, eta, (comp)rs, i);
+    constexpr int U = 2;
+    for (int i0 = threadIdx.x; i0 < nx; i0 += U * blockDim.x) {
+        double cx[U], cxw[U], bx[U], bxw[U], ax[U], axw[U], ay[U], cy[U], by[U], ays[U], cys[U], bys[U], cc[U], Rv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = min(i0 + u * (int)blockDim.x, nx - 1), iw = (i == 0) ? nx - 1 : i - 1;
+            cx[u] = c.cx[i]; cxw[u] = c.cx[iw]; bx[u] = c.bx[i]; bxw[u] = c.bx[iw];
+            ax[u] = c.ax[i]; axw[u] = c.ax[iw]; cc[u] = c.C[i];
+            ay[u] = has_n ? c.ay[i] : 0.0; cy[u] = has_n ? c.cy[i] : 0.0; by[u] = has_n ? c.by[i] : 0.0;
+            ays[u] = has_s ? c.ays[i] : 0.0; cys[u] = has_s ? c.cys[i] : 0.0; bys[u] = has_s ? c.bys[i] : 0.0;
+            Rv[u] = __ldg(M.R + row + i);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = i0 + u * blockDim.x;
+            if (i >= nx) break;
+            const int ie = wrap(i + 1), iw = (i == 0) ? nx - 1 : i - 1;
+            const double xc = pX[i], xe = pX[ie], xw = pX[iw];
+            const double xn = pN[wrap(i + sh[2])], xne = pN[wrap(ie + sh[2])], xnw = pN[wrap(iw + sh[2])];
+            const double xs = pS[wrap(i + sh[0])], xse = pS[wrap(ie + sh[0])], xsw = pS[wrap(iw + sh[0])];
+            double fe = cx[u] * (xn + xne - xs - xse) + bx[u] * (xc + xe) + ax[u] * (xe - xc);
+            double fw = cxw[u] * (xnw + xn - xsw - xs) + bxw[u] * (xw + xc) + axw[u] * (xc - xw);
+            double lphi = fe - fw;
+            if (has_n) lphi += ay[u] * (xn - xc) + cy[u] * (xe + xne - xw - xnw) + by[u] * (xc + xn);
+            if (has_s) lphi -= ays[u] * (xc - xs) + cys[u] * (xse + xe - xsw - xw) + bys[u] * (xs + xc);
+            lphi -= cc[u] * xc;
+            const double rv = lphi - Rv[u];
+            const typename Pol::res rs = (typename Pol::res)rv;
+            v.r[i] = rs;
+            rr += rv * rv;
+            RR += Rv[u] * Rv[u];
+            sb[pidx(i)] = stage0_input(M, v, eta, (comp)rs, i);
+        }
     }
-    part[S_A] += (typename Acc<Pol>::type)rr;
-    part[S_B] += (typename Acc<Pol>::type)RR;
+    part[0] += (typename Acc<Pol>::type)rr;
+    part[1] += (typename Acc<Pol>::type)RR;
     stage0_finish(M, v, j, ws);
 }
 
-template <class Pol>
+template <class Pol, int KM>
 __device__ void phase_le(const MemberDev<Pol> &M, const MemberCtl &c, const RowView<Pol> &v, int j,
-                         unsigned char *ws, typename Acc<Pol>::type (&part)[NSLOT])
+                         unsigned char *ws, typename Acc<Pol>::type (&part)[2 + 2 * KM])
 {
     typedef typename Pol::comp comp;
     typedef typename Pol::vec vec;
@@ -157,27 +173,39 @@ __device__ void phase_le(const MemberDev<Pol> &M, const MemberCtl &c, const RowV
     stencil_row<comp, typename Pol::coef>(stg, stg + nx, stg + 2 * nx, nx, j, ny, coef_of(v), true, (comp *)v.Le,
                                           false);
     SW_TRACE(102);
-    const vec *Lpl[KMAX];
+    const vec *Lpl[KM];
 #pragma unroll
-    for (int l = 0; l < KMAX; ++l) Lpl[l] = v.Lpb + (size_t)phys_slot(c, M.k, l < nd ? l : 0) * v.vstride;
-    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-        const acc_t la = (acc_t)v.Le[i], rv = (acc_t)v.r[i];
-        part[S_A] += la * la;
-        part[S_B] += rv * la;
+    for (int l = 0; l < KM; ++l) Lpl[l] = v.Lpb + (size_t)phys_slot(c, M.k, l < nd ? l : 0) * v.vstride;
+    constexpr int U = batch_of<comp>();
+    for (int i0 = threadIdx.x; i0 < nx; i0 += U * blockDim.x) {
+        acc_t la[U], rv[U], lp[KM][U];
 #pragma unroll
-        for (int l = 0; l < KMAX; ++l) {
-            if (l < nd) {
-                const acc_t lp = (acc_t)Lpl[l][i];
-                part[S_C0 + l] += la * lp;
-                part[S_T0 + l] += rv * lp;
+        for (int u = 0; u < U; ++u) {
+            const int i = min(i0 + u * (int)blockDim.x, nx - 1);
+            la[u] = (acc_t)v.Le[i];
+            rv[u] = (acc_t)v.r[i];
+#pragma unroll
+            for (int l = 0; l < KM; ++l) lp[l][u] = l < nd ? (acc_t)Lpl[l][i] : acc_t(0);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (i0 + u * (int)blockDim.x >= nx) break;
+            part[0] += la[u] * la[u];
+            part[1] += rv[u] * la[u];
+#pragma unroll
+            for (int l = 0; l < KM; ++l) {
+                if (l < nd) {
+                    part[2 + l] += la[u] * lp[l][u];
+                    part[2 + KM + l] += rv[u] * lp[l][u];
+                }
             }
         }
     }
 }
 
-template <class Pol>
+template <class Pol, int KM>
 __device__ void phase_ub(const MemberDev<Pol> &M, const MemberCtl &c, const RowView<Pol> &v,
-                         typename Pol::comp eta, int j, unsigned char *ws, typename Acc<Pol>::type (&part)[NSLOT])
+                         typename Pol::comp eta, int j, unsigned char *ws, typename Acc<Pol>::type (&part)[2 + 2 * KM])
 {
     typedef typename Pol::comp comp;
     typedef typename Pol::vec vec;
@@ -191,10 +219,10 @@ __device__ void phase_ub(const MemberDev<Pol> &M, const MemberCtl &c, const RowV
     row_copy_issue(phr, M.phi + row, nx * 8);
     vec *pn = v.pb + (size_t)phys_slot(c, M.k, nd) * v.vstride;
     vec *Lpn = v.Lpb + (size_t)phys_slot(c, M.k, nd) * v.vstride;
-    const vec *pl[KMAX], *Lpl[KMAX];
-    comp al[KMAX];
+    const vec *pl[KM], *Lpl[KM];
+    comp al[KM];
 #pragma unroll
-    for (int l = 0; l < KMAX; ++l) {
+    for (int l = 0; l < KM; ++l) {
         const size_t off = (size_t)phys_slot(c, M.k, l < nd ? l : 0) * v.vstride;
         pl[l] = v.pb + off;
         Lpl[l] = v.Lpb + off;
@@ -204,36 +232,52 @@ __device__ void phase_ub(const MemberDev<Pol> &M, const MemberCtl &c, const RowV
     const double beta = c.beta;
     const comp beta_c = (comp)beta;
     row_copy_wait();
-    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-        // p_new = e + sum alpha_l p_l and L p_new = L e + sum alpha_l L p_l
-        comp pv = v.el ? v.el[i] : q_load(M, M.e, M.e32, esc, j, i);
-        comp lw = (comp)v.Le[i];
-        comp lps[KMAX];
+    constexpr int U = batch_of<comp>();
+    for (int i0 = threadIdx.x; i0 < nx; i0 += U * blockDim.x) {
+        // loads of the batch: e, L e, r, p_l, L p_l
+        comp ev[U], lev[U], rv[U], pv_l[KM][U], lp_l[KM][U];
 #pragma unroll
-        for (int l = 0; l < KMAX; ++l) {
-            lps[l] = comp(0);
-            if (l < nd) {
-                lps[l] = (comp)Lpl[l][i];
-                pv += al[l] * (comp)pl[l][i];
-                lw += al[l] * lps[l];
+        for (int u = 0; u < U; ++u) {
+            const int i = min(i0 + u * (int)blockDim.x, nx - 1);
+            ev[u] = v.el ? v.el[i] : q_load(M, M.e, M.e32, esc, j, i);
+            lev[u] = (comp)v.Le[i];
+            rv[u] = (comp)v.r[i];
+#pragma unroll
+            for (int l = 0; l < KM; ++l) {
+                pv_l[l][u] = l < nd ? (comp)pl[l][i] : comp(0);
+                lp_l[l][u] = l < nd ? (comp)Lpl[l][i] : comp(0);
             }
         }
-        const vec ps = (vec)pv, ls = (vec)lw;
-        pn[i] = ps;
-        Lpn[i] = ls;
-        // the step: Phi += beta p_new, r += beta L p_new
-        M.phi[row + i] = phr[i] + beta * (double)ps;
-        typename Pol::res rs;
-        if constexpr (Pol::kMixed) rs = v.r[i] + beta_c * ls;
-        else rs = v.r[i] + beta * ls;
-        v.r[i] = rs;
-        const acc_t ra = (acc_t)rs, la = (acc_t)ls;
-        part[S_A] += ra * ra;
-        part[S_B] += la * la;
 #pragma unroll
-        for (int l = 0; l < KMAX; ++l)
-            if (l < nd) part[S_C0 + l] += la * (acc_t)lps[l];
-        sb[pidx(i)] = stage0_input(M, v, eta, (comp)rs, i);
+        for (int u = 0; u < U; ++u) {
+            const int i = i0 + u * blockDim.x;
+            if (i >= nx) break;
+            // p_new = e + sum alpha_l p_l and L p_new = L e + sum alpha_l L p_l
+            comp pv = ev[u], lw = lev[u];
+#pragma unroll
+            for (int l = 0; l < KM; ++l) {
+                if (l < nd) {
+                    pv += al[l] * pv_l[l][u];
+                    lw += al[l] * lp_l[l][u];
+                }
+            }
+            const vec ps = (vec)pv, ls = (vec)lw;
+            pn[i] = ps;
+            Lpn[i] = ls;
+            // the step: Phi += beta p_new, r += beta L p_new
+            M.phi[row + i] = phr[i] + beta * (double)ps;
+            typename Pol::res rs;
+            if constexpr (Pol::kMixed) rs = (typename Pol::res)(rv[u] + beta_c * ls);
+            else rs = rv[u] + beta * ls;
+            v.r[i] = rs;
+            const acc_t ra = (acc_t)rs, la = (acc_t)ls;
+            part[0] += ra * ra;
+            part[1] += la * la;
+#pragma unroll
+            for (int l = 0; l < KM; ++l)
+                if (l < nd) part[2 + l] += la * (acc_t)lp_l[l][u];
+            sb[pidx(i)] = stage0_input(M, v, eta, (comp)rs, i);
+        }
     }
     SW_TRACE(201);
     stage0_finish(M, v, j, ws);
@@ -335,7 +379,9 @@ __device__ void advance(const MemberDev<Pol> &M, MemberCtl &c, const typename Ac
 // ---------------------------------------------------------------------------
 // the persistent GCR kernel
 // ---------------------------------------------------------------------------
-template <class Pol>
+// KM: directions a cycle can hold (k <= KM); it sizes the per-thread
+// registers of the inner-product and update loops
+template <class Pol, int KM>
 __global__ void __launch_bounds__(MAX_THREADS) k_gcr(const EnsDesc *__restrict__ D, int max_nx)
 {
     typedef typename Pol::comp comp;
@@ -384,18 +430,19 @@ __global__ void __launch_bounds__(MAX_THREADS) k_gcr(const EnsDesc *__restrict__
     int par = 0;
     for (int step = 0; s_c.phase != PH_DONE; ++step) {
         SW_TRACE(10 + s_c.phase);
-        acc_t part[NSLOT];
+        constexpr int NP = 2 + 2 * KM;           // A, B, C_0.., T_0..
+        acc_t part[NP];
 #pragma unroll
-        for (int q = 0; q < NSLOT; ++q) part[q] = acc_t(0);
+        for (int q = 0; q < NP; ++q) part[q] = acc_t(0);
         for (int j = j0; j < ny; j += nb) {
             RowView<Pol> v;
             if (j == j0) v = vc;
             else { view_const_global(M, j, v); view_state_global(M, j, v); }
             switch (s_c.phase) {
-            case PH_TRUE: phase_true<Pol>(M, v, eta, j, ws, part); break;
-            case PH_UB: phase_ub<Pol>(M, s_c, v, eta, j, ws, part); break;
+            case PH_TRUE: phase_true<Pol, NP>(M, v, eta, j, ws, part); break;
+            case PH_UB: phase_ub<Pol, KM>(M, s_c, v, eta, j, ws, part); break;
             case PH_PREC: precond_stage<Pol>(M, v, eta, s_c.stage, j, ws); break;
-            case PH_LE: phase_le<Pol>(M, s_c, v, j, ws, part); break;
+            case PH_LE: phase_le<Pol, KM>(M, s_c, v, j, ws, part); break;
             case PH_ZERO:
                 for (int i = threadIdx.x; i < nx; i += blockDim.x) M.phi[(size_t)j * nx + i] = 0.0;
                 break;
@@ -408,8 +455,11 @@ __global__ void __launch_bounds__(MAX_THREADS) k_gcr(const EnsDesc *__restrict__
         const int ns = phase_slots(s_c.phase, s_c.nu + 1, slot);
         acc_t *pbuf = partg + (size_t)par * NSLOT * ny;
         if (ns > 0) {
-            block_sum_many<NSLOT, acc_t>(part, s_blk, scratch);
-            if (threadIdx.x < ns) pbuf[(size_t)threadIdx.x * ny + local] = s_blk[slot[threadIdx.x]];
+            block_sum_many<NP, acc_t>(part, s_blk, scratch);
+            if (threadIdx.x < ns) {
+                const int g = slot[threadIdx.x];          // slot of tot; its place in part
+                pbuf[(size_t)threadIdx.x * ny + local] = s_blk[g < S_T0 ? g : g - S_T0 + 2 + KM];
+            }
         }
         __syncthreads();
         SW_TRACE(31);
@@ -559,44 +609,39 @@ size_t gcr_smem_bytes(int prec, int max_nx, int k, int cache_const, int cache_st
     }
 }
 
-template <class Pol>
-static cudaError_t occupancy_t(int threads, size_t smem, int *blocks_per_sm)
+// the instantiation of k_gcr for a precision and a GCR k
+static const void *gcr_kernel(int prec, int k)
 {
-    if (smem > 227 * 1024 - 8192) { *blocks_per_sm = 0; return cudaSuccess; }
-    cudaError_t e = cudaFuncSetAttribute(k_gcr<Pol>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_gcr<Pol>, threads, smem);
-}
-
-cudaError_t gcr_occupancy(int prec, int threads, size_t smem, int *blocks_per_sm)
-{
+    const bool small = k <= 4;
     switch (prec) {
-    case 0: return occupancy_t<PolFP64>(threads, smem, blocks_per_sm);
-    case 1: return occupancy_t<PolF16>(threads, smem, blocks_per_sm);
-    case 2: return occupancy_t<PolBF16>(threads, smem, blocks_per_sm);
-    default: return cudaErrorInvalidValue;
+    case 0: return small ? (const void *)k_gcr<PolFP64, 4> : (const void *)k_gcr<PolFP64, KMAX>;
+    case 1: return small ? (const void *)k_gcr<PolF16, 4> : (const void *)k_gcr<PolF16, KMAX>;
+    case 2: return small ? (const void *)k_gcr<PolBF16, 4> : (const void *)k_gcr<PolBF16, KMAX>;
+    default: return nullptr;
     }
 }
 
-template <class Pol>
-static cudaError_t launch_gcr_t(const EnsDesc *Ddev, int grid, int max_nx, int threads, size_t smem, cudaStream_t s)
+cudaError_t gcr_occupancy(int prec, int k, int threads, size_t smem, int *blocks_per_sm)
 {
-    cudaError_t e = cudaFuncSetAttribute(k_gcr<Pol>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const void *f = gcr_kernel(prec, k);
+    if (!f) return cudaErrorInvalidValue;
+    if (smem > 227 * 1024 - 8192) { *blocks_per_sm = 0; return cudaSuccess; }
+    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, threads, smem);
+}
+
+cudaError_t launch_gcr(int prec, int k, const EnsDesc *Ddev, int grid, int max_nx, int threads, size_t smem,
+                       cudaStream_t s)
+{
+    const void *f = gcr_kernel(prec, k);
+    if (!f) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const EnsDesc *d = Ddev;
     int mx = max_nx;
     void *args[] = {(void *)&d, (void *)&mx};
-    return cudaLaunchCooperativeKernel((const void *)k_gcr<Pol>, dim3(grid), dim3(threads), args, smem, s);
-}
-
-cudaError_t launch_gcr(int prec, const EnsDesc *Ddev, int grid, int max_nx, int threads, size_t smem, cudaStream_t s)
-{
-    switch (prec) {
-    case 0: return launch_gcr_t<PolFP64>(Ddev, grid, max_nx, threads, smem, s);
-    case 1: return launch_gcr_t<PolF16>(Ddev, grid, max_nx, threads, smem, s);
-    case 2: return launch_gcr_t<PolBF16>(Ddev, grid, max_nx, threads, smem, s);
-    default: return cudaErrorInvalidValue;
-    }
+    return cudaLaunchCooperativeKernel(f, dim3(grid), dim3(threads), args, smem, s);
 }
 
 cudaError_t launch_operator_f64(const OpArgs<double> &a, const double *x, double *y, int threads, cudaStream_t s)
