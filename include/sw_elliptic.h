@@ -68,8 +68,15 @@ typedef enum {
     SW_PC_NONE = 0,             /* option 0: P = I */
     SW_PC_DIAG = 1,             /* option 1: P = D, the diagonal of L */
     SW_PC_DIAG_RICHARDSON = 2,  /* option 2: diagonally preconditioned explicit Richardson */
-    SW_PC_SI_RICHARDSON = 3     /* option 3: semi-implicit Richardson, Eq. 13 */
+    SW_PC_SI_RICHARDSON = 3,    /* option 3: semi-implicit Richardson, Eq. 13 */
+    SW_PC_LEARNED = 4           /* not in the paper: flexible GCR whose
+                                   directions alternate between option 3 and
+                                   a sw_model's network (opts.model), e = s y / d;
+                                   a network direction that does not help is
+                                   replaced by option 3 */
 } sw_precond_kind;
+
+typedef struct sw_model_s *sw_model;  /* opaque, owned by the library */
 
 typedef struct {
     int k;               /* GCR(k): directions kept before a restart (1..8) */
@@ -95,13 +102,19 @@ typedef struct {
                             the initial one), NaN where not reached */
     double *row_residual;/* device, optional (NULL): ny doubles, the final true
                             residual's 2-norm per latitude row */
+    sw_model model;      /* SW_PC_LEARNED: the trained network */
+    double fb_ratio;     /* SW_PC_LEARNED: a network iteration falls back to
+                            option 3 when its direction would remove less of
+                            ||r||^2 than fb_ratio times the share the last
+                            option-3 direction removed (or is not finite);
+                            default 0.5 */
 } sw_solve_opts;
 
 typedef struct {
     int iterations;
     int converged;                 /* 1 if the true residual met tol */
     int status;                    /* sw_status of this solve */
-    int fallbacks;                 /* reserved (learned preconditioner) */
+    int fallbacks;                 /* SW_PC_LEARNED: iterations that fell back to option 3 */
     double r0_norm;                /* ||L(Phi_0) - R||_2 */
     double R_norm;                 /* ||R||_2 */
     double true_rel_residual;      /* ||L(Phi) - R|| / ||R|| at exit, FP64 */
@@ -111,7 +124,8 @@ typedef struct {
 
 /* Fills *o with the defaults: k = 4, tol = 1e-8, max_iters = 1000,
  * min_iters = 0, option 3 with 2 Richardson iterations, automatic eta,
- * omega = 1, FP64, automatic pole band, no periodic true residual. */
+ * omega = 1, FP64, automatic pole band, no periodic true residual, no model,
+ * fb_ratio = 0.5. */
 void sw_solve_opts_default(sw_solve_opts *o);
 
 /* Create a grid of nx x ny points on a sphere of the given radius (m).
@@ -168,6 +182,55 @@ sw_status sw_gcr_solve(sw_grid g, const sw_solve_opts *o, const double *R, doubl
 sw_status sw_ensemble_solve(int n, const sw_grid *grids, const sw_solve_opts *o,
                             const double *const *R, double *const *phi,
                             sw_solve_stats *stats, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Learned preconditioner (no counterpart in the paper).  A three-level U-Net
+ * of 3x3 convolutions (4 -> 32, pool, 32 -> 64, pool, 64 -> 64, up + skip,
+ * 128 -> 64, up + skip, 96 -> 32, 32 -> 1; ReLU after all but the last),
+ * padded like the operator: periodic in longitude, across the poles the pole
+ * row shifted by half a circle.  Weights and activations are BF16, products
+ * accumulate in FP32 on the tensor cores; master weights and AdamW moments
+ * are FP32.  Grid sizes: nx = 64, 128 or a multiple of 256; ny a multiple of
+ * 4 and >= 8.
+ *
+ * Inputs x0 (4 channels) of a residual r on a grid: r / s, the zonal and the
+ * meridional couplings (ax_w + ax_e) / d and (ay_s + ay_n) / d of L's faces,
+ * and sin(latitude), with d = |diag(L)| and s = rms(r).  Output: the network's
+ * y; as a preconditioner e = s y / d, trained on y* = d L^-1(R) / rms(R).
+ * Parameters are one flat FP32 vector of
+ * SW_MODEL_PARAMS values: per layer the weights [out][in][ky][kx], then the
+ * biases.
+ * ------------------------------------------------------------------------- */
+#define SW_MODEL_PARAMS 158369
+
+typedef struct {
+    double lr, beta1, beta2, eps, weight_decay;   /* AdamW; decay on weights only */
+} sw_adamw;
+
+/* Create a model on the current device (parameters zero, AdamW state zero). */
+sw_status sw_model_create(sw_model *out);
+sw_status sw_model_destroy(sw_model m);
+/* Set (and reset the AdamW state) / read the parameters; host, SW_MODEL_PARAMS floats. */
+sw_status sw_model_set_params(sw_model m, const float *params);
+sw_status sw_model_get_params(sw_model m, float *params);
+/* x0 (device FP32 [4][ny][nx]) for the residual r (device FP32 [ny][nx]) on grid g. */
+sw_status sw_model_features(sw_model m, sw_grid g, const float *r, float *x0, void *stream);
+/* y = network(x0) for a batch: x0 device FP32 [batch][4][ny][nx], y device FP32 [batch][ny][nx]. */
+sw_status sw_model_forward(sw_model m, int batch, int ny, int nx, const float *x0, float *y, void *stream);
+/* Mean squared error of y against target (device FP32 [batch][ny][nx]) and
+ * its gradient with respect to the parameters (host, SW_MODEL_PARAMS floats;
+ * NULL to skip); loss: host. */
+sw_status sw_model_loss_grad(sw_model m, int batch, int ny, int nx, const float *x0, const float *target,
+                             double *loss, float *grad, void *stream);
+/* One AdamW step on that loss; loss (host, may be NULL) receives the loss
+ * before the step.  Synchronises the stream only when loss is not NULL. */
+sw_status sw_model_train_step(sw_model m, int batch, int ny, int nx, const float *x0, const float *target,
+                              const sw_adamw *hp, double *loss, void *stream);
+/* e = s y / d: the preconditioner applied to r (device FP32 [ny][nx]). */
+sw_status sw_model_apply(sw_model m, sw_grid g, const float *r, float *e, void *stream);
+/* The inverse scaling, y = d e / s with s = rms(r): the training target of a
+ * pair (r, e = L^-1 r).  Device FP32 [ny][nx] each. */
+sw_status sw_model_target(sw_model m, sw_grid g, const float *r, const float *e, float *y, void *stream);
 
 /* Size of the fixed device scratch used by sw_gcr_solve_noalloc. */
 #define SW_NOALLOC_SCRATCH_BYTES (16u << 20)

@@ -16,7 +16,8 @@ from ._lib import (  # noqa: F401
     SW_OK, SW_ERR_INVALID_ARG, SW_ERR_CUDA, SW_ERR_OOM, SW_ERR_NOT_CONVERGED, SW_ERR_BREAKDOWN,
     SW_ERR_NONFINITE, SW_ERR_TIMEOUT, SW_ERR_INTERNAL,
     SW_PREC_FP64, SW_PREC_MIXED_FP16, SW_PREC_MIXED_BF16, SW_PREC_FP32,
-    SW_PC_NONE, SW_PC_DIAG, SW_PC_DIAG_RICHARDSON, SW_PC_SI_RICHARDSON, SW_NOALLOC_SCRATCH_BYTES,
+    SW_PC_NONE, SW_PC_DIAG, SW_PC_DIAG_RICHARDSON, SW_PC_SI_RICHARDSON, SW_PC_LEARNED, SW_NOALLOC_SCRATCH_BYTES,
+    SW_MODEL_PARAMS, AdamW,
 )
 
 COEFF_KEYS = ("A11", "A12", "A21", "A22", "B1", "B2", "C")
@@ -68,6 +69,8 @@ def sw_solve_opts_default(**overrides) -> SolveOpts:
             raise AttributeError(k)
         if k in ("res_history", "row_residual") and v is not None and not isinstance(v, int):
             v = v.data_ptr()
+        if k == "model" and isinstance(v, Model):
+            v = v.handle.value
         setattr(o, k, v)
     return o
 
@@ -182,3 +185,89 @@ def sw_ensemble_solve(grids: Sequence[Grid], opts: SolveOpts, Rs, phis, stream=N
     _check(load().sw_ensemble_solve(n, hs, C.byref(opts), rp, pp, stats, _stream(stream)),
            "sw_ensemble_solve", SOLVE_OUTCOMES)
     return list(stats)
+
+
+# ---------------------------------------------------------------------------
+# learned preconditioner
+# ---------------------------------------------------------------------------
+class Model:
+    """Handle of a learned-preconditioner network (sw_model); destroyed with the object."""
+
+    def __init__(self):
+        self.handle = C.c_void_p()
+        _check(load().sw_model_create(C.byref(self.handle)), "sw_model_create")
+
+    def __del__(self):
+        if getattr(self, "handle", None) and self.handle.value:
+            try:
+                load().sw_model_destroy(self.handle)
+            except Exception:
+                pass
+            self.handle = C.c_void_p()
+
+
+def sw_model_set_params(m: Model, params) -> None:
+    import numpy as np
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    if p.size != SW_MODEL_PARAMS:
+        raise ValueError(f"expected {SW_MODEL_PARAMS} parameters, got {p.size}")
+    _check(load().sw_model_set_params(m.handle, p.ctypes.data), "sw_model_set_params")
+
+
+def sw_model_get_params(m: Model):
+    import numpy as np
+    p = np.empty(SW_MODEL_PARAMS, dtype=np.float32)
+    _check(load().sw_model_get_params(m.handle, p.ctypes.data), "sw_model_get_params")
+    return p
+
+
+def sw_model_features(m: Model, g: Grid, r, x0, stream=None) -> None:
+    import torch
+    _check(load().sw_model_features(m.handle, g.handle, _ptr(r, torch.float32, (g.ny, g.nx)),
+                                    _ptr(x0, torch.float32, (4, g.ny, g.nx)), _stream(stream)), "sw_model_features")
+
+
+def sw_model_forward(m: Model, x0, y, stream=None) -> None:
+    import torch
+    B, _, ny, nx = x0.shape
+    _check(load().sw_model_forward(m.handle, B, ny, nx, _ptr(x0, torch.float32, (B, 4, ny, nx)),
+                                   _ptr(y, torch.float32, (B, ny, nx)), _stream(stream)), "sw_model_forward")
+
+
+def sw_model_loss_grad(m: Model, x0, target, want_grad: bool = True, stream=None):
+    import numpy as np
+    import torch
+    B, _, ny, nx = x0.shape
+    loss = C.c_double()
+    g = np.empty(SW_MODEL_PARAMS, dtype=np.float32) if want_grad else None
+    _check(load().sw_model_loss_grad(m.handle, B, ny, nx, _ptr(x0, torch.float32, (B, 4, ny, nx)),
+                                     _ptr(target, torch.float32, (B, ny, nx)), C.byref(loss),
+                                     g.ctypes.data if g is not None else None, _stream(stream)),
+           "sw_model_loss_grad")
+    return loss.value, g
+
+
+def sw_model_train_step(m: Model, x0, target, lr: float, beta1: float = 0.9, beta2: float = 0.999,
+                        eps: float = 1e-8, weight_decay: float = 0.0, want_loss: bool = True, stream=None):
+    import torch
+    B, _, ny, nx = x0.shape
+    hp = AdamW(lr, beta1, beta2, eps, weight_decay)
+    loss = C.c_double()
+    _check(load().sw_model_train_step(m.handle, B, ny, nx, _ptr(x0, torch.float32, (B, 4, ny, nx)),
+                                      _ptr(target, torch.float32, (B, ny, nx)), C.byref(hp),
+                                      C.byref(loss) if want_loss else None, _stream(stream)),
+           "sw_model_train_step")
+    return loss.value if want_loss else None
+
+
+def sw_model_apply(m: Model, g: Grid, r, e, stream=None) -> None:
+    import torch
+    _check(load().sw_model_apply(m.handle, g.handle, _ptr(r, torch.float32, (g.ny, g.nx)),
+                                 _ptr(e, torch.float32, (g.ny, g.nx)), _stream(stream)), "sw_model_apply")
+
+
+def sw_model_target(m: Model, g: Grid, r, e, y, stream=None) -> None:
+    import torch
+    shp = (g.ny, g.nx)
+    _check(load().sw_model_target(m.handle, g.handle, _ptr(r, torch.float32, shp), _ptr(e, torch.float32, shp),
+                                  _ptr(y, torch.float32, shp), _stream(stream)), "sw_model_target")

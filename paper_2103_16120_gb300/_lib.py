@@ -17,15 +17,18 @@ STATUS_NAMES = {0: "SW_OK", 1: "SW_ERR_INVALID_ARG", 2: "SW_ERR_CUDA", 3: "SW_ER
                 4: "SW_ERR_NOT_CONVERGED", 5: "SW_ERR_BREAKDOWN", 6: "SW_ERR_NONFINITE",
                 7: "SW_ERR_TIMEOUT", 8: "SW_ERR_INTERNAL"}
 SW_PREC_FP64, SW_PREC_MIXED_FP16, SW_PREC_MIXED_BF16, SW_PREC_FP32 = range(4)
-SW_PC_NONE, SW_PC_DIAG, SW_PC_DIAG_RICHARDSON, SW_PC_SI_RICHARDSON = range(4)
+SW_PC_NONE, SW_PC_DIAG, SW_PC_DIAG_RICHARDSON, SW_PC_SI_RICHARDSON, SW_PC_LEARNED = range(5)
 
 # every symbol the header declares (checked by the CPU test-suite)
 EXPORTS = (
     "sw_solve_opts_default", "sw_grid_create", "sw_grid_destroy", "sw_grid_workspace_bytes",
     "sw_grid_attach_workspace", "sw_elliptic_set_coeffs", "sw_grid_set_eta", "sw_grid_get_eta",
     "sw_operator_apply", "sw_precond_apply", "sw_gcr_solve", "sw_ensemble_solve", "sw_gcr_solve_noalloc",
-    "sw_last_error",
+    "sw_last_error", "sw_model_create", "sw_model_destroy", "sw_model_set_params", "sw_model_get_params",
+    "sw_model_features", "sw_model_forward", "sw_model_loss_grad", "sw_model_train_step", "sw_model_apply",
+    "sw_model_target",
 )
+SW_MODEL_PARAMS = 158369
 SW_NOALLOC_SCRATCH_BYTES = 16 << 20
 
 
@@ -34,7 +37,8 @@ class SolveOpts(C.Structure):
                 ("pc", C.c_int), ("n_richardson", C.c_int), ("eta", C.c_double), ("omega", C.c_double),
                 ("prec", C.c_int), ("pole_band_rows", C.c_int), ("ru_every", C.c_int),
                 ("threads_per_row", C.c_int),
-                ("res_history", C.c_void_p), ("row_residual", C.c_void_p)]
+                ("res_history", C.c_void_p), ("row_residual", C.c_void_p),
+                ("model", C.c_void_p), ("fb_ratio", C.c_double)]
 
 
 class SolveStats(C.Structure):
@@ -45,6 +49,11 @@ class SolveStats(C.Structure):
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class AdamW(C.Structure):
+    _fields_ = [("lr", C.c_double), ("beta1", C.c_double), ("beta2", C.c_double), ("eps", C.c_double),
+                ("weight_decay", C.c_double)]
 
 
 _lib = None
@@ -74,6 +83,18 @@ def load() -> C.CDLL:
     lib.sw_gcr_solve_noalloc.argtypes = [vp, C.POINTER(SolveOpts), vp, vp, C.POINTER(SolveStats), vp]
     lib.sw_ensemble_solve.argtypes = [i, C.POINTER(vp), C.POINTER(SolveOpts), C.POINTER(vp),
                                       C.POINTER(vp), C.POINTER(SolveStats), vp]
+    fp = C.POINTER(C.c_float)
+    lib.sw_model_create.argtypes = [C.POINTER(vp)]
+    lib.sw_model_destroy.argtypes = [vp]
+    lib.sw_model_set_params.argtypes = [vp, vp]
+    lib.sw_model_get_params.argtypes = [vp, vp]
+    lib.sw_model_features.argtypes = [vp, vp, vp, vp, vp]
+    lib.sw_model_forward.argtypes = [vp, i, i, i, vp, vp, vp]
+    lib.sw_model_loss_grad.argtypes = [vp, i, i, i, vp, vp, C.POINTER(d), vp, vp]
+    lib.sw_model_train_step.argtypes = [vp, i, i, i, vp, vp, C.POINTER(AdamW), C.POINTER(d), vp]
+    lib.sw_model_apply.argtypes = [vp, vp, vp, vp, vp]
+    lib.sw_model_target.argtypes = [vp, vp, vp, vp, vp, vp]
+    del fp
     lib.sw_last_error.argtypes = []
     lib.sw_last_error.restype = C.c_char_p
     for name in EXPORTS:

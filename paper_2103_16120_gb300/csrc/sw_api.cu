@@ -21,6 +21,8 @@ static sw_status fail(sw_status st, const std::string &msg)
     return st;
 }
 
+sw_status sw::api_fail(sw_status st, const char *msg) { return fail(st, msg); }
+
 static sw_status cuda_fail(cudaError_t e, const char *where)
 {
     return fail(e == cudaErrorMemoryAllocation ? SW_ERR_OOM : SW_ERR_CUDA,
@@ -55,6 +57,11 @@ struct sw_grid_s {
     double *h_eta;
 };
 
+GridView sw::grid_view(const sw_grid_s *g)
+{
+    return GridView{g->nx, g->ny, g->device, g->sms, g->wax, g->way, g->wdiag};
+}
+
 // threads of the block that works on one row: about four values per thread,
 // at least nx/16 (the tridiagonal chunks live in registers, 16 values at most)
 static int row_threads(int nx, int requested = 0)
@@ -84,6 +91,7 @@ extern "C" void sw_solve_opts_default(sw_solve_opts *o)
     o->prec = SW_PREC_FP64;
     o->pole_band_rows = -1;
     o->ru_every = 0;
+    o->fb_ratio = 0.5;
 }
 
 extern "C" const char *sw_last_error(void) { return g_err.c_str(); }
@@ -177,8 +185,13 @@ static sw_status check_opts(const sw_solve_opts *o, bool solve)
 {
     if (!o) return fail(SW_ERR_INVALID_ARG, "options are NULL");
     if (o->k < 1 || o->k > KMAX) return fail(SW_ERR_INVALID_ARG, "k must be 1..8");
-    if (o->pc < 0 || o->pc > 3) return fail(SW_ERR_INVALID_ARG, "pc must be 0..3");
-    if ((o->pc == 2 || o->pc == 3) && (o->n_richardson < 1 || o->n_richardson > 16))
+    if (o->pc < 0 || o->pc > 4) return fail(SW_ERR_INVALID_ARG, "pc must be 0..4");
+    if (o->pc == SW_PC_LEARNED) {
+        if (!solve) return fail(SW_ERR_INVALID_ARG, "the learned preconditioner is applied by sw_model_apply");
+        if (!o->model) return fail(SW_ERR_INVALID_ARG, "SW_PC_LEARNED needs opts.model");
+        if (!(o->fb_ratio >= 0.0) || !std::isfinite(o->fb_ratio)) return fail(SW_ERR_INVALID_ARG, "fb_ratio must be >= 0");
+    }
+    if (o->pc >= 2 && (o->n_richardson < 1 || o->n_richardson > 16))
         return fail(SW_ERR_INVALID_ARG, "n_richardson must be 1..16");
     if (o->prec < 0 || o->prec > 2) return fail(SW_ERR_INVALID_ARG, "prec must be FP64, MIXED_FP16 or MIXED_BF16");
     if (solve) {
@@ -327,7 +340,8 @@ static void fill_member(sw_grid g, const sw_solve_opts *o, const double *R, doub
     WsLayout L = ws_layout(g, o->prec, o->k);
     char *w = (char *)g->ws;
     M.nx = g->nx; M.ny = g->ny; M.k = o->k; M.pc = o->pc;
-    M.nstages = (o->pc == 2 || o->pc == 3) ? o->n_richardson : 1;
+    M.nstages = o->pc >= 2 ? o->n_richardson : 1;     // the learned option falls back to option 3
+    M.fb_ratio = o->fb_ratio;
     M.min_iters = o->min_iters; M.max_iters = o->max_iters; M.ru_every = o->ru_every;
     M.band = pole_band(g, o);
     M.tol = o->tol; M.omega = o->omega; M.etap = g->eta;
@@ -380,6 +394,7 @@ static sw_status upload_member(sw_grid g, const sw_solve_opts *o, const double *
 extern "C" sw_status sw_precond_apply(sw_grid g, const sw_solve_opts *o, const void *r, void *q, void *stream)
 {
     if (!g || !r || !q) return fail(SW_ERR_INVALID_ARG, "sw_precond_apply: NULL argument");
+    if (o && o->pc == SW_PC_LEARNED) return fail(SW_ERR_INVALID_ARG, "sw_precond_apply: use sw_model_apply for SW_PC_LEARNED");
     if (!g->has_coeffs) return fail(SW_ERR_INVALID_ARG, "sw_precond_apply: coefficients not set");
     sw_status st = check_opts(o, false);
     if (st) return st;
@@ -393,7 +408,7 @@ extern "C" sw_status sw_precond_apply(sw_grid g, const sw_solve_opts *o, const v
     }
     if ((st = ensure_ws(g, o->prec, o->k))) return st;
     alignas(16) unsigned char hbuf[sizeof(SolverBlock::dev)];
-    int nst = (o->pc == 2 || o->pc == 3) ? o->n_richardson : 1;
+    int nst = o->pc >= 2 ? o->n_richardson : 1;
     if (o->prec == SW_PREC_FP64) {
         MemberDev<PolFP64> M;
         fill_member<PolFP64>(g, o, nullptr, nullptr, M);
@@ -428,6 +443,10 @@ static sw_status solve_members(int n, const sw_grid *grids, const sw_solve_opts 
     sw_status st = check_opts(o, true);
     if (st) return st;
     if (n < 1 || n > MAX_MEMBERS) return fail(SW_ERR_INVALID_ARG, "number of members must be 1..480");
+    if (o->pc == SW_PC_LEARNED) {
+        if (n != 1) return fail(SW_ERR_INVALID_ARG, "SW_PC_LEARNED solves one grid per call");
+        if ((st = model_check_grid(grids[0]))) return st;
+    }
     int dev = -1;
     CK(cudaGetDevice(&dev));
     int max_nx = 0;
@@ -476,7 +495,9 @@ static sw_status solve_members(int n, const sw_grid *grids, const sw_solve_opts 
     const int levels[3][2] = {{1, 1}, {1, 0}, {0, 0}};
     long rows_total = 0;
     for (int m = 0; m < n; ++m) rows_total += grids[m]->ny;
-    for (int lv = 0; lv < 3 && !grid; ++lv) {
+    // the learned preconditioner ends a launch before every application of
+    // the network, so the owner-only vectors cannot live in shared memory
+    for (int lv = (o->pc == SW_PC_LEARNED ? 1 : 0); lv < 3 && !grid; ++lv) {
         const size_t sm_l = gcr_smem_bytes(o->prec, max_nx, o->k, levels[lv][0], levels[lv][1]);
         int bps = 0;
         CK(gcr_occupancy(o->prec, o->k, threads, sm_l, &bps));
@@ -521,6 +542,24 @@ static sw_status solve_members(int n, const sw_grid *grids, const sw_solve_opts 
     }
     CK(cudaMemcpyAsync(lead->desc, &D, sizeof(EnsDesc), cudaMemcpyHostToDevice, s));
     CK(launch_gcr(o->prec, o->k, lead->desc, grid, max_nx, threads, smem, s));
+    if (o->pc == SW_PC_LEARNED) {
+        // flexible GCR: a launch ends where the next direction is the
+        // network's; the network runs on r, its output becomes e, and the
+        // solver resumes with L(e)
+        sw_grid g = grids[0];
+        float *ef = model_scratch(o->model, g->ny, g->nx);
+        if (!ef) return fail(SW_ERR_OOM, "learned preconditioner: buffers");
+        const void *r = (const char *)g->ws + ws_layout(g, o->prec, o->k).r;
+        for (int guard = 0; guard <= o->max_iters + 2; ++guard) {
+            CK(cudaMemcpyAsync(g->h_ctl, &g->blk->ctl, sizeof(MemberCtl), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            if (g->h_ctl->phase != PH_EXT) break;
+            if ((st = model_precondition(o->model, g, r, o->prec == SW_PREC_FP64, ef, s))) return st;
+            CK(launch_store_e(o->prec, g->blk->dev, ef, g->nx, g->ny, row_threads(g->nx, o->threads_per_row), s));
+            CK(cudaMemsetAsync(&g->blk->g, 0, sizeof(GlobalCtl), s));
+            CK(launch_gcr(o->prec, o->k, lead->desc, grid, max_nx, threads, smem, s));
+        }
+    }
     for (int m = 0; m < n; ++m) {
         sw_grid g = grids[m];
         CK(cudaMemcpyAsync(g->h_ctl, &g->blk->ctl, sizeof(MemberCtl) + sizeof(GlobalCtl), cudaMemcpyDeviceToHost, s));
@@ -539,6 +578,7 @@ static sw_status solve_members(int n, const sw_grid *grids, const sw_solve_opts 
             sw_solve_stats &S = stats[m];
             std::memset(&S, 0, sizeof(S));
             S.iterations = c.it;
+            S.fallbacks = c.fallbacks;
             S.status = mst;
             S.converged = (mst == SW_OK);
             S.r0_norm = c.r0;
@@ -594,6 +634,8 @@ extern "C" sw_status sw_gcr_solve_noalloc(sw_grid g, const sw_solve_opts *o, con
     if (!g || !R || !phi) return fail(SW_ERR_INVALID_ARG, "sw_gcr_solve_noalloc: NULL argument");
     sw_status st = check_opts(o, true);
     if (st) return st;
+    if (o->pc == SW_PC_LEARNED)
+        return fail(SW_ERR_INVALID_ARG, "sw_gcr_solve_noalloc: the learned preconditioner needs its own buffers");
     if (!g->has_coeffs) return fail(SW_ERR_INVALID_ARG, "sw_gcr_solve_noalloc: coefficients not set");
     int dev = -1;
     CK(cudaGetDevice(&dev));

@@ -22,7 +22,11 @@ constexpr int MAX_NX = 4096;
 constexpr int MAX_THREADS = 256;    // block size of the row kernels
 
 // phase kinds of the GCR state machine (see sw_solver.cu)
-enum Phase : int { PH_TRUE = 0, PH_UB = 1, PH_PREC = 2, PH_LE = 3, PH_ZERO = 5, PH_DONE = 6 };
+enum Phase : int { PH_TRUE = 0, PH_UB = 1, PH_PREC = 2, PH_LE = 3, PH_ZERO = 5, PH_DONE = 6,
+                   PH_EXT = 7,    // learned preconditioner: the launch ends, the host applies the network
+                   PH_PREC0 = 8   // first stage of option 3 from r (a learned iteration falling back)
+};
+constexpr int PC_LEARNED = 4;
 
 // status codes (mirror sw_status)
 enum : int { ST_OK = 0, ST_INVALID = 1, ST_CUDA = 2, ST_OOM = 3, ST_NOT_CONVERGED = 4,
@@ -85,6 +89,7 @@ struct MemberDev {
     int nx, ny;
     int k, pc, nstages, min_iters, max_iters, ru_every, band;
     double tol, omega;
+    double fb_ratio;                // learned preconditioner: fallback threshold
     const double *etap;             // device: eta of the factorised zonal operators
     // FP64 face coefficients (true residual): face x (i+1/2, j): ax = a11/dlam^2,
     // cx = a12/(4 dlam dphi), bx = b1/(2 dlam); face y (i, j+1/2): ay = a22/dphi^2,
@@ -114,7 +119,11 @@ struct MemberDev {
 // global copy holds the initial state (from the host) and the final one.
 struct MemberCtl {
     int phase, stage, it, nu, base, init, status, pad_;
+    int fb_now, fallbacks;          // learned preconditioner: this iteration fell back; count
+    int net_turn, pad2_;            // learned preconditioner: the next direction is the network's
     double beta, nR, r0, rn_rec, rn_true;
+    double rn_cur;                  // ||r|| of the residual the next direction works on
+    double g3;                      // share of ||r||^2 the last option-3 direction removed
     double alpha[KMAX + 1];
     double G[KMAX + 1][KMAX + 1];   // Gram matrix <L p_l, L p_m> of the cycle (logical)
 };

@@ -5,6 +5,11 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 
+#include "../../include/sw_elliptic.h"
+
+struct sw_grid_s;
+struct sw_model_s;
+
 namespace sw {
 
 struct EnsDesc;
@@ -43,7 +48,25 @@ cudaError_t launch_operator_f32(const OpArgs<float> &a, const float *x, float *y
 cudaError_t launch_precond(int prec, const void *Mdev, int nx, int ny, int nstages, void *qout, int threads,
                            cudaStream_t s);
 cudaError_t launch_fill(double *p, size_t n, double v, cudaStream_t s);
+// the member's e from an FP32 field (the network's direction)
+cudaError_t launch_store_e(int prec, const void *Mdev, const float *ef, int nx, int ny, int threads, cudaStream_t s);
+// the learned preconditioner applied to the residual r (FP64 or FP32) of
+// grid g, e (FP32 [ny][nx]) into the model's buffer, whose address is returned
+sw_status model_precondition(::sw_model_s *m, const ::sw_grid_s *g, const void *r, bool r64, float *e,
+                             cudaStream_t s);
+sw_status model_check_grid(const ::sw_grid_s *g);
+float *model_scratch(::sw_model_s *m, int ny, int nx);
 size_t member_dev_bytes(int prec);
+// set the calling thread's error message and return st (sw_api.cu)
+sw_status api_fail(sw_status st, const char *msg);
+
+// what the learned preconditioner reads from a grid handle (sw_api.cu)
+struct GridView {
+    int nx, ny, device, sms;
+    const float *wax, *way, *wdiag;   // FP32 zonal / meridional face coefficients, diag(L)
+};
+GridView grid_view(const ::sw_grid_s *g);
+
 // the fixed scratch of sw_gcr_solve_noalloc on the current device (sw_static.cu)
 cudaError_t noalloc_scratch(void **ptr, size_t *bytes);
 

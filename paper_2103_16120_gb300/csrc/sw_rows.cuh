@@ -382,7 +382,7 @@ __device__ void stage0_finish(const MemberDev<Pol> &M, const RowView<Pol> &v, in
     comp *sm = (comp *)(ws + red_offset<Pol>(M.nx));
     __syncthreads();
     SW_TRACE(401);
-    if (M.pc == 3) trisolve_view(sb, M.nx, v, sm);
+    if (M.pc >= 3) trisolve_view(sb, M.nx, v, sm);     // option 3 (also the learned fallback)
     SW_TRACE(402);
     if (M.nstages == 1) q_store_row(M, M.e, M.e32, M.e_s, j, sb, v.el, (float *)sm);
     else q_store_row(M, M.qa, M.qa32, M.qa_s, j, sb, (comp *)nullptr, (float *)sm);
@@ -411,7 +411,7 @@ __device__ void precond_stage(const MemberDev<Pol> &M, const RowView<Pol> &v, ty
     stage3_q(ws, M, ih, if32, is, j);
     SW_TRACE(301);
     const comp *S = stg, *X = stg + nx, *N = stg + 2 * nx;
-    const bool opt3 = (M.pc == 3);
+    const bool opt3 = (M.pc >= 3);
     stencil_row<comp, typename Pol::coef>(S, X, N, nx, j, ny, coef_of(v), !opt3, sb, true);
     constexpr int U = batch_of<comp>();
     for (int i0 = threadIdx.x; i0 < nx; i0 += U * blockDim.x) {

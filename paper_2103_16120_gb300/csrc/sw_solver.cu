@@ -283,6 +283,17 @@ __device__ void phase_ub(const MemberDev<Pol> &M, const MemberCtl &c, const RowV
     stage0_finish(M, v, j, ws);
 }
 
+// first stage of option 3 from the stored r (a learned iteration falling back)
+template <class Pol>
+__device__ void phase_prec0(const MemberDev<Pol> &M, const RowView<Pol> &v, typename Pol::comp eta, int j,
+                            unsigned char *ws)
+{
+    typedef typename Pol::comp comp;
+    comp *sb = (comp *)(ws + sb_offset<Pol>(M.nx));
+    for (int i = threadIdx.x; i < M.nx; i += blockDim.x) sb[pidx(i)] = stage0_input(M, v, eta, (comp)v.r[i], i);
+    stage0_finish(M, v, j, ws);
+}
+
 // ---------------------------------------------------------------------------
 // state transition after a phase, from the member-wide sums tot[slot].  The
 // scalars (alpha, beta, the Gram update, norms) are computed in the policy's
@@ -298,7 +309,15 @@ __device__ void advance(const MemberDev<Pol> &M, MemberCtl &c, const typename Ac
     // exit test keeps that margin below the tolerance
     const double tolR = M.tol * c.nR * (Pol::kMixed ? (1.0 - 1e-5) : 1.0);
     bool done = false;
-    auto to_precond = [&]() { c.stage = 1; c.phase = (M.nstages > 1) ? PH_PREC : PH_LE; };
+    // the learned preconditioner alternates its directions with option 3's:
+    // on the network's turn the launch ends (PH_EXT), the host writes the
+    // network's e, and the next launch resumes with L(e)
+    const bool learned = (M.pc == PC_LEARNED);
+    auto to_precond = [&]() {
+        c.stage = 1;
+        if (learned && c.net_turn && !c.fb_now) c.phase = PH_EXT;
+        else c.phase = M.nstages > 1 ? PH_PREC : PH_LE;
+    };
     auto finish = [&](int st) { c.status = st; done = true; };
     switch (c.phase) {
     case PH_TRUE: {
@@ -307,7 +326,7 @@ __device__ void advance(const MemberDev<Pol> &M, MemberCtl &c, const typename Ac
             c.init = 0;
             c.nR = sqrt((double)tot[S_B]);
             c.r0 = rn;
-            c.rn_true = c.rn_rec = rn;
+            c.rn_true = c.rn_rec = c.rn_cur = rn;
             c.nu = -1;
             if (writer && M.hist) M.hist[0] = c.nR > 0.0 ? rn / c.nR : 0.0;
             if (c.nR == 0.0) { c.phase = PH_ZERO; break; }
@@ -315,7 +334,7 @@ __device__ void advance(const MemberDev<Pol> &M, MemberCtl &c, const typename Ac
             if (rn <= M.tol * c.nR * (Pol::kMixed ? (1.0 - 1e-5) : 1.0) && M.min_iters <= 0) { finish(ST_OK); break; }
             to_precond();
         } else {
-            c.rn_true = rn;
+            c.rn_true = c.rn_cur = rn;
             if (writer && M.hist) M.hist[c.it] = rn / c.nR;
             if (!isfinite(rn)) { finish(ST_NONFINITE); break; }
             if (rn <= tolR && c.it >= M.min_iters) { finish(ST_OK); break; }
@@ -327,6 +346,10 @@ __device__ void advance(const MemberDev<Pol> &M, MemberCtl &c, const typename Ac
     case PH_PREC:
         c.stage += 1;
         if (c.stage >= M.nstages) c.phase = PH_LE;
+        break;
+    case PH_PREC0:
+        c.stage = 1;
+        c.phase = M.nstages > 1 ? PH_PREC : PH_LE;
         break;
     case PH_LE: {
         // alpha_l of the text; <Lp_new, Lp_new> and <r, Lp_new> of the
@@ -340,6 +363,18 @@ __device__ void advance(const MemberDev<Pol> &M, MemberCtl &c, const typename Ac
             rlp += a[l] * tot[S_T0 + l];
             c.alpha[l] = (double)a[l];
         }
+        if (learned && c.net_turn && !c.fb_now) {
+            // the network's direction would remove rlp^2 / lplp of ||r||^2; it
+            // must remove at least fb_ratio times the share the last option-3
+            // direction removed, else this iteration takes option 3
+            const double gain = (double)rlp * (double)rlp / ((double)lplp * c.rn_cur * c.rn_cur);
+            if (!(lplp > sc(0)) || !isfinite(lplp) || !isfinite(rlp) || !(gain >= M.fb_ratio * c.g3)) {
+                c.fb_now = 1;
+                c.fallbacks += 1;
+                c.phase = PH_PREC0;
+                break;
+            }
+        }
         if (!(lplp > sc(0)) || !isfinite(lplp) || !isfinite(rlp)) { finish(ST_BREAKDOWN); break; }
         c.beta = (double)(-rlp / lplp);
         c.phase = PH_UB;
@@ -349,7 +384,11 @@ __device__ void advance(const MemberDev<Pol> &M, MemberCtl &c, const typename Ac
         const int ln = nd;                        // logical index of the new direction
         c.it += 1;
         const double rn = sqrt((double)tot[S_A]);
-        c.rn_rec = rn;
+        if (learned && (!c.net_turn || c.fb_now) && c.rn_cur > 0.0)
+            c.g3 = 1.0 - (rn / c.rn_cur) * (rn / c.rn_cur);      // an option-3 direction
+        c.rn_rec = c.rn_cur = rn;
+        c.fb_now = 0;
+        if (learned) c.net_turn ^= 1;
         if (writer && M.hist) M.hist[c.it] = rn / c.nR;
         c.G[ln][ln] = (double)tot[S_B];
         for (int m = 0; m < ln; ++m) c.G[ln][m] = c.G[m][ln] = (double)tot[S_C0 + m];
@@ -408,6 +447,10 @@ __global__ void __launch_bounds__(MAX_THREADS) k_gcr(const EnsDesc *__restrict__
     copy_in(&s_M, mdev<Pol>(B));
     copy_in(&s_c, &B->ctl);
     __syncthreads();
+    // a launch that follows the host's application of the network resumes
+    // with L(e); every block makes the same change
+    if (threadIdx.x == 0 && s_c.phase == PH_EXT) s_c.phase = PH_LE;
+    __syncthreads();
     const MemberDev<Pol> &M = s_M;
     const int ny = M.ny, nx = M.nx;
     unsigned char *ws = dsm;
@@ -428,7 +471,7 @@ __global__ void __launch_bounds__(MAX_THREADS) k_gcr(const EnsDesc *__restrict__
     acc_t *partg = (acc_t *)M.part;
     bool ok = true;
     int par = 0;
-    for (int step = 0; s_c.phase != PH_DONE; ++step) {
+    for (int step = 0; s_c.phase != PH_DONE && s_c.phase != PH_EXT; ++step) {
         SW_TRACE(10 + s_c.phase);
         constexpr int NP = 2 + 2 * KM;           // A, B, C_0.., T_0..
         acc_t part[NP];
@@ -442,6 +485,7 @@ __global__ void __launch_bounds__(MAX_THREADS) k_gcr(const EnsDesc *__restrict__
             case PH_TRUE: phase_true<Pol, NP>(M, v, eta, j, ws, part); break;
             case PH_UB: phase_ub<Pol, KM>(M, s_c, v, eta, j, ws, part); break;
             case PH_PREC: precond_stage<Pol>(M, v, eta, s_c.stage, j, ws); break;
+            case PH_PREC0: phase_prec0<Pol>(M, v, eta, j, ws); break;
             case PH_LE: phase_le<Pol, KM>(M, s_c, v, j, ws, part); break;
             case PH_ZERO:
                 for (int i = threadIdx.x; i < nx; i += blockDim.x) M.phi[(size_t)j * nx + i] = 0.0;
@@ -512,7 +556,7 @@ __global__ void __launch_bounds__(MAX_THREADS) k_gcr(const EnsDesc *__restrict__
         for (int q = 0; q < (int)(sizeof(MemberCtl) / 4); ++q) dst[q] = src[q];
     }
     // per-row norms of the final true residual
-    if (ok && M.rowres && (s_c.status == ST_OK || s_c.status == ST_NOT_CONVERGED)) {
+    if (ok && s_c.phase == PH_DONE && M.rowres && (s_c.status == ST_OK || s_c.status == ST_NOT_CONVERGED)) {
         for (int j = j0; j < ny; j += nb) {
             const typename Pol::res *r = (j == j0) ? vc.r : M.r + (size_t)j * nx;
             double t = 0.0;
@@ -573,6 +617,23 @@ __global__ void __launch_bounds__(MAX_THREADS) k_precond(const MemberDev<Pol> *M
     } else {
         precond_stage<Pol>(M, v, eta, mu, j, dsm);
     }
+}
+
+// e of the member from an FP32 field (the network's direction), stored like
+// the last preconditioner stage: FP64, or 16-bit with the row scale (FP32 on
+// the pole-band rows)
+template <class Pol>
+__global__ void __launch_bounds__(MAX_THREADS) k_store_e(const MemberDev<Pol> *Mp, const float *ef)
+{
+    typedef typename Pol::comp comp;
+    extern __shared__ __align__(16) unsigned char dsm[];
+    const MemberDev<Pol> &M = *Mp;
+    const int j = blockIdx.x, nx = M.nx;
+    comp *sb = (comp *)(dsm + sb_offset<Pol>(nx));
+    float *scratch = (float *)(dsm + red_offset<Pol>(nx));
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) sb[pidx(i)] = (comp)ef[(size_t)j * nx + i];
+    __syncthreads();
+    q_store_row(M, M.e, M.e32, M.e_s, j, sb, (comp *)nullptr, scratch);
 }
 
 // dequantise the preconditioner output e into q (mixed policies)
@@ -682,6 +743,26 @@ cudaError_t launch_precond(int prec, const void *Mdev, int nx, int ny, int nstag
     case 0: return launch_precond_t<PolFP64>(Mdev, nx, ny, nstages, nullptr, threads, s);
     case 1: return launch_precond_t<PolF16>(Mdev, nx, ny, nstages, (float *)qout, threads, s);
     case 2: return launch_precond_t<PolBF16>(Mdev, nx, ny, nstages, (float *)qout, threads, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <class Pol>
+static cudaError_t store_e_t(const void *Mdev, const float *ef, int nx, int ny, int threads, cudaStream_t s)
+{
+    const size_t smem = work_bytes<Pol>(nx);
+    cudaError_t e = cudaFuncSetAttribute(k_store_e<Pol>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_store_e<Pol><<<ny, threads, smem, s>>>((const MemberDev<Pol> *)Mdev, ef);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_store_e(int prec, const void *Mdev, const float *ef, int nx, int ny, int threads, cudaStream_t s)
+{
+    switch (prec) {
+    case 0: return store_e_t<PolFP64>(Mdev, ef, nx, ny, threads, s);
+    case 1: return store_e_t<PolF16>(Mdev, ef, nx, ny, threads, s);
+    case 2: return store_e_t<PolBF16>(Mdev, ef, nx, ny, threads, s);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -13,5 +13,5 @@ lambda_i = 2*pi*i/nx (longitude contiguous).
 from .sphere import grid_coords, real_sh, random_sh_field  # noqa: F401
 from .shallow_water import (  # noqa: F401
     EARTH, SWState, synthetic_state, coefficients, rhs_divergence, problem,
-    sequence_problem, ensemble_members,
+    sequence_problem, ensemble_members, random_rhs,
 )

@@ -187,3 +187,21 @@ def ensemble_members(spec=((32, 128, 64), (24, 256, 128), (8, 512, 256)), config
             out.append((nx, ny, 1000 * config + k))
             k += 1
     return out
+
+
+def random_rhs(nx: int, ny: int, seed: int, n: int) -> np.ndarray:
+    """n seeded right-hand sides [n, ny, nx] of unit RMS, from smooth to rough:
+    white noise whose 2-D spectrum is damped by (1 + (k / k0)^2)^(-p/2) with a
+    random corner k0 (2..nx/4 wavenumbers) and slope p (0..3) per field."""
+    rng = np.random.default_rng(seed + 104729)
+    ky = np.fft.fftfreq(ny) * ny
+    kx = np.fft.rfftfreq(nx) * nx
+    kk = np.sqrt(ky[:, None] ** 2 + kx[None, :] ** 2)
+    out = np.empty((n, ny, nx))
+    for q in range(n):
+        k0 = math.exp(rng.uniform(math.log(2.0), math.log(nx / 4)))
+        p = rng.uniform(0.0, 3.0)
+        spec = np.fft.rfft2(rng.standard_normal((ny, nx))) * (1.0 + (kk / k0) ** 2) ** (-p / 2)
+        f = np.fft.irfft2(spec, s=(ny, nx))
+        out[q] = f / math.sqrt(float(np.mean(f * f)))
+    return out
