@@ -16,6 +16,18 @@ before timing; successive steps read different sets, so the inputs of the
 timed region are larger than L2.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                  [--workload seq512|learned256|ensemble64|large2048]
+
+The default workload is the one above.  The others measure the remaining
+configurations on one GPU, one JSON line each:
+  learned256  the learned preconditioner at 256 x 128: GPU training on solver
+              generated triples (tensor-core throughput against the BF16
+              peak), then flexible-GCR solves against option 3 at 256 x 128
+              and, without retraining, at 1024 x 512
+  ensemble64  64 independent members (32 at 128x64, 24 at 256x128, 8 at
+              512x256) in one persistent launch, against the same members
+              solved one launch each
+  large2048   solves of a 2048 x 1024 sequence, mixed against FP64
 """
 from __future__ import annotations
 
@@ -350,17 +362,248 @@ def run_gpu(args):
         torch.distributed.destroy_process_group()
 
 
+# ---------------------------------------------------------------------------
+# further workloads (one GPU)
+# ---------------------------------------------------------------------------
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def _grid(sw, torch, P, dev):
+    ny, nx = P["C"].shape
+    g = sw.sw_grid_create(nx, ny)
+    sw.sw_elliptic_set_coeffs(g, *[torch.as_tensor(P[k], device=dev) for k in KEYS])
+    return g
+
+
+def _time_solves(sw, torch, g, opts, Rs, reps):
+    """Mean solve time (CUDA events) and mean iterations over reps solves."""
+    stream = torch.cuda.current_stream()
+    tot, its, fb = 0.0, 0, 0
+    for q in range(reps):
+        R = Rs[q % len(Rs)]
+        phi = torch.zeros_like(R)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        st = sw.sw_gcr_solve(g, opts, R, phi)
+        b.record(stream)
+        torch.cuda.synchronize()
+        if st.status != sw.SW_OK:
+            raise RuntimeError(f"solve failed: {st.as_dict()}")
+        tot += a.elapsed_time(b)
+        its += st.iterations
+        fb += st.fallbacks
+    return tot / reps, its / reps, fb / reps
+
+
+def run_learned(args):
+    import torch
+    import paper_2103_16120_gb300 as sw
+    from paper_2103_16120_gb300 import build as swb, learned
+    swb.build()
+    dev = torch.device("cuda", 0)
+    nx, ny = 256, 128
+    n_states, per_state = max(1, args.samples // 40), 40
+    t0 = time.perf_counter()
+    probs = [synth.problem(nx, ny, 3_000_000 + s) for s in range(n_states)]
+    rhs = np.stack([synth.random_rhs(nx, ny, 3_000_000 + s, per_state) for s in range(n_states)])
+    m = sw.Model()
+    sw.sw_model_set_params(m, learned.init_params(1))
+    x0, tg = learned.make_dataset(m, probs, rhs)
+    t_data = time.perf_counter() - t0
+    # training throughput: K timed AdamW steps of batch 32 after W warm-up steps
+    B = 32
+    n = x0.shape[0]
+    stream = torch.cuda.current_stream()
+    learned.train(m, x0, tg, steps=args.warmup, batch=B, lr=1e-3)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    learned.train(m, x0, tg, steps=args.steps, batch=B, lr=1e-3, seed=1)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms_step = a.elapsed_time(b) / args.steps
+    # then train to the end of the epochs asked for
+    epochs_steps = max(0, args.epochs * n // B - args.steps - args.warmup)
+    losses = learned.train(m, x0, tg, steps=epochs_steps, batch=B, lr=2e-3, seed=2) if epochs_steps else []
+    flops = learned.train_flops_per_point() * nx * ny * B
+    tflops = flops / (ms_step * 1e-3) / 1e12
+    peak = _peaks().get("bf16_tflops", 1900.0)
+    out = {}
+    for (gx, gy) in ((256, 128), (1024, 512)):
+        Ps = [synth.problem(gx, gy, 4_000_000 + s) for s in range(2)]
+        res = {}
+        for tag, kw in (("option3", {}), ("learned", {"pc": sw.SW_PC_LEARNED, "model": m})):
+            o = sw.sw_solve_opts_default(k=K_GCR, tol=TOL, prec=sw.SW_PREC_MIXED_FP16, max_iters=2000, **kw)
+            ms, its, fb = 0.0, 0.0, 0.0
+            for P in Ps:
+                g = _grid(sw, torch, P, dev)
+                R = torch.as_tensor(P["R"], device=dev)
+                _time_solves(sw, torch, g, o, [R], 1)
+                a_, b_, c_ = _time_solves(sw, torch, g, o, [R], 3)
+                ms += a_ / len(Ps); its += b_ / len(Ps); fb += c_ / len(Ps)
+            res[tag] = {"solves_per_s": 1e3 / ms, "ms_per_solve": ms, "mean_iterations": its, "mean_fallbacks": fb}
+        out[f"{gx}x{gy}"] = res
+    head = out["256x128"]["learned"]
+    print(json.dumps({
+        "metric": METRIC, "value": head["solves_per_s"], "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": head["ms_per_solve"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16 network (f32 accumulate), f32/f16 solver", "data": "synthetic",
+        "config": {"workload": "learned preconditioner at 256x128 (config 3)", "samples": n,
+                   "epochs": args.epochs, "batch": B, "network": "3-level U-Net 32/64/64, 158369 parameters"},
+        "solves": out,
+        "training": {"ms_per_step": ms_step, "samples_per_s": B / (ms_step * 1e-3), "tflops": tflops,
+                     "data_generation_s": t_data, "final_loss": losses[-1][1] if losses else None},
+        "roofline": {"bound": "tensor", "achieved": tflops, "peak": peak, "unit": "TFLOP/s",
+                     "frac": tflops / peak, "traffic": None,
+                     "kernel": "training step (k_conv / k_wgrad, mma.sync BF16)",
+                     "note": "algorithmic FLOPs of forward + input and weight gradients per step / step time",
+                     "peak_source": "MEASURED_PEAKS.json bf16_tflops (of measured)"},
+        "cpu_baseline": None, "gpu_launches": None,
+    }), flush=True)
+
+
+def run_ensemble(args):
+    import torch
+    import paper_2103_16120_gb300 as sw
+    from paper_2103_16120_gb300 import build as swb
+    swb.build()
+    dev = torch.device("cuda", 0)
+    members = synth.ensemble_members()
+    Ps = [synth.problem(nx, ny, seed) for nx, ny, seed in members]
+    grids = [_grid(sw, torch, P, dev) for P in Ps]
+    Rs = [torch.as_tensor(P["R"], device=dev) for P in Ps]
+    phis = [torch.zeros_like(R) for R in Rs]
+    o = sw.sw_solve_opts_default(k=K_GCR, tol=TOL, prec=sw.SW_PREC_MIXED_FP16, max_iters=2000)
+    stream = torch.cuda.current_stream()
+
+    def one(batched: bool):
+        for p in phis:
+            p.zero_()
+        if batched:
+            return sw.sw_ensemble_solve(grids, o, Rs, phis)
+        return [sw.sw_gcr_solve(g, o, R, p) for g, R, p in zip(grids, Rs, phis)]
+
+    res = {}
+    for tag, batched in (("one_launch", True), ("launch_per_member", False)):
+        for _ in range(args.warmup):
+            one(batched)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.steps):
+            sts = one(batched)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / args.steps
+        bad = [s.as_dict() for s in sts if s.status != sw.SW_OK]
+        if bad:
+            raise RuntimeError(f"ensemble member failed: {bad[0]}")
+        res[tag] = {"ms_per_ensemble": ms, "member_solves_per_s": len(grids) / (ms * 1e-3),
+                    "iterations": [s.iterations for s in sts]}
+    head = res["one_launch"]
+    pts_its = sum(nx * ny * it for (nx, ny, _), it in zip(members, head["iterations"]))
+    bytes_ = algorithmic_bytes_per_point(True, 1) - algorithmic_bytes_per_point(True, 0)
+    achieved = bytes_ * pts_its / (head["ms_per_ensemble"] * 1e-3) / 1e9
+    peak = _peaks().get("hbm_gbs", 6800.0)
+    print(json.dumps({
+        "metric": METRIC, "value": head["member_solves_per_s"], "unit": "solves/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_ensemble"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 (f16 storage, f64 reductions)",
+        "data": "synthetic",
+        "config": {"workload": "ensemble of 64 members in one persistent launch (config 2)",
+                   "members": "32 x 128x64, 24 x 256x128, 8 x 512x256", "tol": TOL, "precision": "mixed-fp16"},
+        "launch_per_member": res["launch_per_member"], "one_launch": head,
+        "speedup_vs_launch_per_member": res["launch_per_member"]["ms_per_ensemble"] / head["ms_per_ensemble"],
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "kernel": "k_gcr<PolF16> (all members, one launch)",
+                     "note": "algorithmic bytes (172 B per point per iteration) / ensemble time",
+                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
+        "cpu_baseline": None, "gpu_launches": 1 * args.steps,
+    }), flush=True)
+
+
+def run_large(args):
+    import torch
+    import paper_2103_16120_gb300 as sw
+    from paper_2103_16120_gb300 import build as swb
+    swb.build()
+    dev = torch.device("cuda", 0)
+    nx, ny = 2048, 1024
+    n = args.warmup + args.steps
+    seq = [synth.sequence_problem(nx, ny, 4000, t) for t in range(n)]
+    g = sw.sw_grid_create(nx, ny)
+    stream = torch.cuda.current_stream()
+    res = {}
+    for tag, prec in (("fp64", sw.SW_PREC_FP64), ("mixed", sw.SW_PREC_MIXED_FP16)):
+        o = sw.sw_solve_opts_default(k=K_GCR, tol=TOL, prec=prec, max_iters=4000)
+        phi = torch.zeros((ny, nx), dtype=torch.float64, device=dev)
+        tot, its, sol = 0.0, 0, None
+        for t, P in enumerate(seq):
+            sw.sw_elliptic_set_coeffs(g, *[torch.as_tensor(P[k], device=dev) for k in KEYS])
+            R = torch.as_tensor(P["R"], device=dev)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            st = sw.sw_gcr_solve(g, o, R, phi)
+            b.record(stream)
+            torch.cuda.synchronize()
+            if st.status != sw.SW_OK:
+                raise RuntimeError(f"solve failed: {st.as_dict()}")
+            if t >= args.warmup:
+                tot += a.elapsed_time(b)
+                its += st.iterations
+        res[tag] = {"ms_per_solve": tot / args.steps, "solves_per_s": 1e3 * args.steps / tot,
+                    "mean_iterations": its / args.steps, "phi": phi}
+    # reference for the error: the FP64 GPU solve of the last problem to 1e-13
+    o = sw.sw_solve_opts_default(k=K_GCR, tol=1e-13, prec=sw.SW_PREC_FP64, max_iters=8000)
+    ref = res["fp64"]["phi"].clone()
+    sw.sw_gcr_solve(g, o, torch.as_tensor(seq[-1]["R"], device=dev), ref)
+    err = float(torch.linalg.norm(res["mixed"]["phi"] - ref) / torch.linalg.norm(ref))
+    mixed = res["mixed"]
+    bpp = algorithmic_bytes_per_point(True, mixed["mean_iterations"])
+    achieved = bpp * nx * ny / (mixed["ms_per_solve"] * 1e-3) / 1e9
+    peak = _peaks().get("hbm_gbs", 6800.0)
+    print(json.dumps({
+        "metric": METRIC, "value": mixed["solves_per_s"], "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": mixed["ms_per_solve"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 (f16 storage, f64 reductions)", "data": "synthetic",
+        "config": {"workload": "2048x1024 solve sequence, warm start (config 4)", "tol": TOL, "k": K_GCR},
+        "fp64_gcr": {k: v for k, v in res["fp64"].items() if k != "phi"},
+        "mixed": {k: v for k, v in mixed.items() if k != "phi"},
+        "speedup_vs_fp64": mixed["solves_per_s"] / res["fp64"]["solves_per_s"],
+        "solution_rel_error_vs_fp64_gpu_1e-13": err,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "kernel": "k_gcr<PolF16>",
+                     "note": "algorithmic bytes of one solve / solve time",
+                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
+        "cpu_baseline": None, "gpu_launches": 3 * args.steps,
+    }), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gcr", choices=["gcr", "reference"])
+    ap.add_argument("--workload", default="seq512", choices=["seq512", "learned256", "ensemble64", "large2048"])
+    ap.add_argument("--samples", type=int, default=20000, help="learned256: training triples")
+    ap.add_argument("--epochs", type=int, default=4, help="learned256: training epochs")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "learned256":
+        run_learned(args)
+    elif args.workload == "ensemble64":
+        run_ensemble(args)
+    elif args.workload == "large2048":
+        run_large(args)
     else:
         run_gpu(args)
 

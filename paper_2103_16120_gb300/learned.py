@@ -81,3 +81,26 @@ def train(model: Model, x0, target, steps: int, batch: int, lr: float, seed: int
         if want:
             losses.append((s, loss))
     return losses
+
+
+LAYERS = ((4, 32), (32, 64), (64, 64), (128, 64), (96, 32), (32, 1))   # (in, out) channels per 3x3 layer
+
+
+def init_params(seed: int) -> np.ndarray:
+    """He-normal weights and zero biases, flat in the library's order (per
+    layer the weights [out][in][3][3], then the biases)."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for ci, co in LAYERS:
+        parts.append((rng.standard_normal((co, ci, 3, 3)) * math.sqrt(2.0 / (9 * ci))).ravel())
+        parts.append(np.zeros(co))
+    return np.concatenate(parts).astype(np.float32)
+
+
+def train_flops_per_point() -> float:
+    """Algorithmic FLOPs of one training step per grid point of a sample:
+    forward, input gradients of layers 2..6, weight gradients of all layers
+    (unpadded channels; 2 FLOPs per multiply-add)."""
+    level = (0, 1, 2, 1, 0, 0)
+    per = [2.0 * 9 * ci * co / 4 ** l for (ci, co), l in zip(LAYERS, level)]
+    return sum(per) + sum(per[1:]) + sum(per)
