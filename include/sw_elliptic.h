@@ -183,6 +183,20 @@ sw_status sw_ensemble_solve(int n, const sw_grid *grids, const sw_solve_opts *o,
                             const double *const *R, double *const *phi,
                             sw_solve_stats *stats, void *stream);
 
+/* sw_ensemble_solve without host synchronisation: every step is enqueued on
+ * `stream` and the call returns at once.  stats_dev (device, n entries, may
+ * be NULL) receives the members' sw_solve_stats when the solve completes on
+ * the stream; the return value reports only argument and enqueue errors.
+ * Nothing is allocated once each grid's workspace exists, i.e. after one
+ * solve with the same precision and k (or an attached workspace), so the
+ * call can then be recorded in a CUDA graph and replayed.  A replay uses the
+ * member descriptors of the recorded call, which each grid keeps in pinned
+ * host memory until its next sw_ensemble_solve_async.  Not for
+ * SW_PC_LEARNED. */
+sw_status sw_ensemble_solve_async(int n, const sw_grid *grids, const sw_solve_opts *o,
+                                  const double *const *R, double *const *phi,
+                                  sw_solve_stats *stats_dev, void *stream);
+
 /* ---------------------------------------------------------------------------
  * Learned preconditioner (no counterpart in the paper).  A three-level U-Net
  * of 3x3 convolutions (4 -> 32, pool, 32 -> 64, pool, 64 -> 64, up + skip,

@@ -163,6 +163,33 @@ def sw_gcr_solve(g: Grid, opts: SolveOpts, R, phi, stream=None) -> SolveStats:
     return st
 
 
+def sw_ensemble_solve_async(grids: Sequence[Grid], opts: SolveOpts, Rs, phis, stats_dev=None, stream=None) -> None:
+    """Enqueue an ensemble solve without synchronising; stats_dev: a device
+    buffer of len(grids) * sizeof(SolveStats) bytes (torch uint8) or None;
+    read it with stats_from_device."""
+    import torch
+    n = len(grids)
+    hs = (C.c_void_p * n)(*[g.handle.value for g in grids])
+    rp = (C.c_void_p * n)(*[_ptr(R, torch.float64, (g.ny, g.nx)).value for g, R in zip(grids, Rs)])
+    pp = (C.c_void_p * n)(*[_ptr(p, torch.float64, (g.ny, g.nx)).value for g, p in zip(grids, phis)])
+    if stats_dev is not None and stats_dev.numel() < n * C.sizeof(SolveStats):
+        raise ValueError("stats_dev too small")
+    _check(load().sw_ensemble_solve_async(n, hs, C.byref(opts), rp, pp,
+                                          None if stats_dev is None else C.c_void_p(stats_dev.data_ptr()),
+                                          _stream(stream)), "sw_ensemble_solve_async")
+
+
+def stats_buffer(n: int):
+    import torch
+    return torch.zeros(n * C.sizeof(SolveStats), dtype=torch.uint8, device="cuda")
+
+
+def stats_from_device(buf, n: int) -> list:
+    raw = bytes(buf.cpu().numpy().tobytes())
+    arr = (SolveStats * n).from_buffer_copy(raw[: n * C.sizeof(SolveStats)])
+    return list(arr)
+
+
 def sw_gcr_solve_noalloc(g: Grid, opts: SolveOpts, R, phi, stream=None) -> SolveStats:
     """sw_gcr_solve with the work vectors in the library's fixed device scratch
     (no allocation; grids up to SW_NOALLOC_SCRATCH_BYTES of workspace)."""

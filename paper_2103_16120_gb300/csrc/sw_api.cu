@@ -53,6 +53,7 @@ struct sw_grid_s {
     EnsDesc *desc;                 // device: launch descriptor when this grid leads a launch
     EnsDesc *h_desc;               // pinned host staging of desc
     MemberCtl *h_ctl;              // pinned host copies read after a solve
+    void *h_mdev;                  // pinned staging of the member descriptor (async solves)
     GlobalCtl *h_g;
     double *h_eta;
 };
@@ -117,11 +118,13 @@ extern "C" sw_status sw_grid_create(int nx, int ny, double radius, sw_grid *out)
     if (e == cudaSuccess) e = cudaMalloc((void **)&g->desc, sizeof(EnsDesc));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&g->h_desc, sizeof(EnsDesc));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&g->h_ctl, sizeof(MemberCtl) + sizeof(GlobalCtl) + 64);
+    if (e == cudaSuccess) e = cudaMallocHost(&g->h_mdev, sizeof(SolverBlock::dev));
     if (e != cudaSuccess) {
         if (g->cmem) cudaFree(g->cmem);
         if (g->blk) cudaFree(g->blk);
         if (g->desc) cudaFree(g->desc);
         if (g->h_desc) cudaFreeHost(g->h_desc);
+        if (g->h_ctl) cudaFreeHost(g->h_ctl);
         delete g;
         return cuda_fail(e, "sw_grid_create");
     }
@@ -149,6 +152,7 @@ extern "C" sw_status sw_grid_destroy(sw_grid g)
     cudaFreeHost(g->h_desc);
     if (g->ws_owned && g->ws) cudaFree(g->ws);
     cudaFreeHost(g->h_ctl);
+    cudaFreeHost(g->h_mdev);
     delete g;
     return SW_OK;
 }
@@ -437,6 +441,99 @@ extern "C" sw_status sw_precond_apply(sw_grid g, const sw_solve_opts *o, const v
 // ---------------------------------------------------------------------------
 // solves
 // ---------------------------------------------------------------------------
+// Launch shape of one persistent launch: every member owns a group of blocks
+// and every block one latitude row when the co-resident blocks suffice, so
+// the row's constant data and owner-only vectors stay in shared memory;
+// otherwise the co-resident blocks are shared out in proportion to each
+// member's expected work (points times nx: the iteration count grows about
+// linearly with the resolution) and cycle over several rows each, with
+// everything in global memory.
+struct Plan {
+    int grid = 0, cc = 0, cs = 0, threads = 0;
+    size_t smem = 0;
+    std::vector<int> nb;
+};
+
+static sw_status plan_launch(int n, const sw_grid *grids, const sw_solve_opts *o, int max_nx, Plan &P)
+{
+    const int sms = grids[0]->sms;
+    P.threads = row_threads(max_nx, o->threads_per_row);
+    P.nb.assign(n, 1);
+    const int levels[3][2] = {{1, 1}, {1, 0}, {0, 0}};
+    long rows_total = 0;
+    for (int m = 0; m < n; ++m) rows_total += grids[m]->ny;
+    // the learned preconditioner ends a launch before every application of
+    // the network, so the owner-only vectors cannot live in shared memory
+    for (int lv = (o->pc == SW_PC_LEARNED ? 1 : 0); lv < 3 && !P.grid; ++lv) {
+        const size_t sm_l = gcr_smem_bytes(o->prec, max_nx, o->k, levels[lv][0], levels[lv][1]);
+        int bps = 0;
+        CK(gcr_occupancy(o->prec, o->k, P.threads, sm_l, &bps));
+        if (bps > 0 && rows_total <= (long)bps * sms) {
+            for (int m = 0; m < n; ++m) P.nb[m] = grids[m]->ny;
+            P.grid = (int)rows_total; P.cc = levels[lv][0]; P.cs = levels[lv][1]; P.smem = sm_l;
+        }
+    }
+    if (!P.grid) {
+        P.smem = gcr_smem_bytes(o->prec, max_nx, o->k, 0, 0);
+        P.cc = P.cs = 0;
+        int bps = 0;
+        CK(gcr_occupancy(o->prec, o->k, P.threads, P.smem, &bps));
+        if (bps < 1) return fail(SW_ERR_INVALID_ARG, "grid rows too long for the solver kernel");
+        const int cap = bps * sms;
+        if (n > cap) return fail(SW_ERR_INVALID_ARG, "too many members for one launch on this device");
+        int used = n;
+        while (used < cap) {
+            int best = -1;
+            double bw = 0.0;
+            for (int m = 0; m < n; ++m) {
+                if (P.nb[m] >= grids[m]->ny) continue;
+                const double wgt = (double)grids[m]->ny * grids[m]->nx * grids[m]->nx / P.nb[m];
+                if (wgt > bw) { bw = wgt; best = m; }
+            }
+            if (best < 0) break;
+            ++P.nb[best];
+            ++used;
+        }
+        P.grid = used;
+    }
+    return SW_OK;
+}
+
+static void fill_desc(EnsDesc &D, int n, const sw_grid *grids, const Plan &P)
+{
+    D.n = n;
+    D.grid = P.grid;
+    D.cache_const = P.cc;
+    D.cache_state = P.cs;
+    D.cta_begin[0] = 0;
+    for (int m = 0; m < n; ++m) {
+        D.cta_begin[m + 1] = D.cta_begin[m] + P.nb[m];
+        D.blk[m] = grids[m]->blk;
+    }
+}
+
+static sw_status check_members(int n, const sw_grid *grids, const sw_solve_opts *o, const double *const *R,
+                               double *const *phi, int &max_nx)
+{
+    if (n < 1 || n > MAX_MEMBERS) return fail(SW_ERR_INVALID_ARG, "number of members must be 1..480");
+    int dev = -1;
+    CK(cudaGetDevice(&dev));
+    max_nx = 0;
+    for (int m = 0; m < n; ++m) {
+        sw_grid g = grids[m];
+        if (!g) return fail(SW_ERR_INVALID_ARG, "NULL grid in the member list");
+        if (!R[m] || !phi[m]) return fail(SW_ERR_INVALID_ARG, "NULL R or phi");
+        if (!g->has_coeffs) return fail(SW_ERR_INVALID_ARG, "coefficients not set for a member grid");
+        if (g->device != dev) return fail(SW_ERR_INVALID_ARG, "member grid belongs to another device");
+        for (int q = 0; q < m; ++q)
+            if (grids[q] == g) return fail(SW_ERR_INVALID_ARG, "the member grids must be distinct");
+        if (n > 1 && (o->res_history || o->row_residual))
+            return fail(SW_ERR_INVALID_ARG, "res_history / row_residual are for single solves");
+        max_nx = std::max(max_nx, g->nx);
+    }
+    return SW_OK;
+}
+
 static sw_status solve_members(int n, const sw_grid *grids, const sw_solve_opts *o, const double *const *R,
                                double *const *phi, sw_solve_stats *stats, cudaStream_t s)
 {
@@ -483,63 +580,15 @@ static sw_status solve_members(int n, const sw_grid *grids, const sw_solve_opts 
     }
     if (o->res_history) CK(launch_fill(o->res_history, (size_t)o->max_iters + 1, NAN, s));
 
-    // Launch shape: every member owns a group of blocks and every block one
-    // latitude row when the co-resident blocks suffice, so the row's constant
-    // data and owner-only vectors stay in shared memory; otherwise the blocks
-    // cycle over several rows with everything in global memory.
-    const int sms = grids[0]->sms;
-    const int threads = row_threads(max_nx, o->threads_per_row);
-    std::vector<int> nb(n, 1);
-    int grid = 0, cc = 0, cs = 0;
-    size_t smem = 0;
-    const int levels[3][2] = {{1, 1}, {1, 0}, {0, 0}};
-    long rows_total = 0;
-    for (int m = 0; m < n; ++m) rows_total += grids[m]->ny;
-    // the learned preconditioner ends a launch before every application of
-    // the network, so the owner-only vectors cannot live in shared memory
-    for (int lv = (o->pc == SW_PC_LEARNED ? 1 : 0); lv < 3 && !grid; ++lv) {
-        const size_t sm_l = gcr_smem_bytes(o->prec, max_nx, o->k, levels[lv][0], levels[lv][1]);
-        int bps = 0;
-        CK(gcr_occupancy(o->prec, o->k, threads, sm_l, &bps));
-        if (bps > 0 && rows_total <= (long)bps * sms) {
-            for (int m = 0; m < n; ++m) nb[m] = grids[m]->ny;
-            grid = (int)rows_total; cc = levels[lv][0]; cs = levels[lv][1]; smem = sm_l;
-        }
-    }
-    if (!grid) {
-        // several rows per block: spread the co-resident blocks over the members
-        smem = gcr_smem_bytes(o->prec, max_nx, o->k, 0, 0);
-        int bps = 0;
-        CK(gcr_occupancy(o->prec, o->k, threads, smem, &bps));
-        if (bps < 1) return fail(SW_ERR_INVALID_ARG, "grid rows too long for the solver kernel");
-        const int cap = bps * sms;
-        if (n > cap) return fail(SW_ERR_INVALID_ARG, "too many members for one launch on this device");
-        int used = n;
-        while (used < cap) {
-            int best = -1;
-            double bw = 0.0;
-            for (int m = 0; m < n; ++m) {
-                if (nb[m] >= grids[m]->ny) continue;
-                double wgt = (double)grids[m]->ny * grids[m]->nx / nb[m];
-                if (wgt > bw) { bw = wgt; best = m; }
-            }
-            if (best < 0) break;
-            ++nb[best];
-            ++used;
-        }
-        grid = used;
-    }
+    Plan P;
+    if ((st = plan_launch(n, grids, o, max_nx, P))) return st;
+    const int threads = P.threads, grid = P.grid, cc = P.cc, cs = P.cs;
+    const size_t smem = P.smem;
+    const std::vector<int> &nb = P.nb;
+    (void)cc; (void)cs; (void)nb;
     sw_grid lead = grids[0];
     EnsDesc &D = *lead->h_desc;
-    D.n = n;
-    D.grid = grid;
-    D.cache_const = cc;
-    D.cache_state = cs;
-    D.cta_begin[0] = 0;
-    for (int m = 0; m < n; ++m) {
-        D.cta_begin[m + 1] = D.cta_begin[m] + nb[m];
-        D.blk[m] = grids[m]->blk;
-    }
+    fill_desc(D, n, grids, P);
     CK(cudaMemcpyAsync(lead->desc, &D, sizeof(EnsDesc), cudaMemcpyHostToDevice, s));
     CK(launch_gcr(o->prec, o->k, lead->desc, grid, max_nx, threads, smem, s));
     if (o->pc == SW_PC_LEARNED) {
@@ -729,4 +778,53 @@ extern "C" sw_status sw_gcr_solve_noalloc(sw_grid g, const sw_solve_opts *o, con
     case SW_ERR_NONFINITE: return fail(SW_ERR_NONFINITE, "non-finite residual norm");
     default: return fail(SW_ERR_INTERNAL, "solver ended in an unexpected state");
     }
+}
+
+// ---------------------------------------------------------------------------
+// ensemble solve without host synchronisation
+// ---------------------------------------------------------------------------
+extern "C" sw_status sw_ensemble_solve_async(int n, const sw_grid *grids, const sw_solve_opts *o,
+                                             const double *const *R, double *const *phi,
+                                             sw_solve_stats *stats_dev, void *stream)
+{
+    if (!grids || !R || !phi) return fail(SW_ERR_INVALID_ARG, "sw_ensemble_solve_async: NULL argument");
+    sw_status st = check_opts(o, true);
+    if (st) return st;
+    if (o->pc == SW_PC_LEARNED)
+        return fail(SW_ERR_INVALID_ARG, "sw_ensemble_solve_async: the learned preconditioner needs the host");
+    int max_nx = 0;
+    if ((st = check_members(n, grids, o, R, phi, max_nx))) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int m = 0; m < n; ++m) {
+        sw_grid g = grids[m];
+        if (o->eta > 0.0 && o->eta != g->eta_explicit) {
+            g->eta_explicit = o->eta;
+            if ((st = refactor(g, s))) return st;
+        }
+        if ((st = ensure_ws(g, o->prec, o->k))) return st;
+        if (o->prec == SW_PREC_FP64) {
+            MemberDev<PolFP64> M;
+            fill_member<PolFP64>(g, o, R[m], phi[m], M);
+            std::memcpy(g->h_mdev, &M, sizeof(M));
+        } else if (o->prec == SW_PREC_MIXED_FP16) {
+            MemberDev<PolF16> M;
+            fill_member<PolF16>(g, o, R[m], phi[m], M);
+            std::memcpy(g->h_mdev, &M, sizeof(M));
+        } else {
+            MemberDev<PolBF16> M;
+            fill_member<PolBF16>(g, o, R[m], phi[m], M);
+            std::memcpy(g->h_mdev, &M, sizeof(M));
+        }
+        CK(cudaMemcpyAsync(g->blk->dev, g->h_mdev, member_dev_bytes(o->prec), cudaMemcpyHostToDevice, s));
+    }
+    if (o->res_history) CK(launch_fill(o->res_history, (size_t)o->max_iters + 1, NAN, s));
+    Plan P;
+    if ((st = plan_launch(n, grids, o, max_nx, P))) return st;
+    sw_grid lead = grids[0];
+    fill_desc(*lead->h_desc, n, grids, P);
+    CK(cudaMemcpyAsync(lead->desc, lead->h_desc, sizeof(EnsDesc), cudaMemcpyHostToDevice, s));
+    CK(launch_init_members(lead->desc, n, s));
+    CK(launch_gcr(o->prec, o->k, lead->desc, P.grid, max_nx, P.threads, P.smem, s));
+    if (stats_dev) CK(launch_member_stats(lead->desc, n, stats_dev, s));
+    return SW_OK;
 }

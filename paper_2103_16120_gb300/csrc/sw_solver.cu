@@ -767,6 +767,56 @@ cudaError_t launch_store_e(int prec, const void *Mdev, const float *ef, int nx, 
     }
 }
 
+__global__ void k_init_members(const EnsDesc *D)
+{
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= D->n) return;
+    SolverBlock *B = D->blk[m];
+    MemberCtl c = {};
+    c.phase = PH_TRUE;
+    c.init = 1;
+    c.nu = -1;
+    B->ctl = c;
+    B->g.count = 0;
+    B->g.abort = 0;
+    B->g.where = 0;
+}
+
+__global__ void k_member_stats(const EnsDesc *D, sw_solve_stats *out)
+{
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= D->n) return;
+    const SolverBlock *B = D->blk[m];
+    const MemberCtl &c = B->ctl;
+    // the members' descriptors share their leading fields whatever the policy
+    const MemberDev<PolFP64> *M = (const MemberDev<PolFP64> *)B->dev;
+    const bool timeout = B->g.abort != 0;
+    const int st = timeout ? ST_TIMEOUT : (c.phase == PH_DONE ? c.status : ST_INTERNAL);
+    sw_solve_stats S = {};
+    S.iterations = c.it;
+    S.converged = (st == ST_OK);
+    S.status = st;
+    S.fallbacks = c.fallbacks;
+    S.r0_norm = c.r0;
+    S.R_norm = c.nR;
+    S.true_rel_residual = c.nR > 0 ? c.rn_true / c.nR : 0.0;
+    S.recursive_rel_residual = c.nR > 0 ? c.rn_rec / c.nR : 0.0;
+    S.eta = *M->etap;
+    out[m] = S;
+}
+
+cudaError_t launch_init_members(const EnsDesc *Ddev, int n, cudaStream_t s)
+{
+    k_init_members<<<(n + 127) / 128, 128, 0, s>>>(Ddev);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_member_stats(const EnsDesc *Ddev, int n, sw_solve_stats *out, cudaStream_t s)
+{
+    k_member_stats<<<(n + 127) / 128, 128, 0, s>>>(Ddev, out);
+    return cudaGetLastError();
+}
+
 #ifdef SW_PHASE_TRACE
 // configure the device timeline (traced builds only): buffer of 2*cap words
 extern "C" void sw_trace_configure(unsigned long long *buf, int cap, int block)

@@ -1,0 +1,92 @@
+"""Ensembles in one persistent launch: the asynchronous entry point, its
+capture in a CUDA graph, and the launch-shape autotuner, each against the
+synchronous sw_ensemble_solve on the same members (same kernel, same launch
+shape, fixed reduction orders: equal results)."""
+import numpy as np
+import pytest
+
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2103_16120_gb300 as sw  # noqa: E402
+from paper_2103_16120_gb300 import autotune  # noqa: E402
+
+MEMBERS = [(128, 64, 9001), (128, 64, 9002), (256, 128, 9003), (130, 33, 9004), (512, 256, 9005)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _build():
+    from paper_2103_16120_gb300 import build
+    build.build()
+    assert torch.cuda.is_available()
+
+
+def members():
+    Ps = [synth.problem(nx, ny, seed) for nx, ny, seed in MEMBERS]
+    grids = []
+    for (nx, ny, _), P in zip(MEMBERS, Ps):
+        g = sw.sw_grid_create(nx, ny)
+        sw.sw_elliptic_set_coeffs(g, *[torch.as_tensor(P[k], device="cuda") for k in sw.COEFF_KEYS])
+        grids.append(g)
+    Rs = [torch.as_tensor(P["R"], device="cuda") for P in Ps]
+    return grids, Rs
+
+
+@pytest.mark.parametrize("prec", [sw.SW_PREC_FP64, sw.SW_PREC_MIXED_FP16])
+def test_async_equals_sync(prec):
+    grids, Rs = members()
+    o = sw.sw_solve_opts_default(prec=prec, tol=1e-8)
+    ref = [torch.zeros_like(R) for R in Rs]
+    sts = sw.sw_ensemble_solve(grids, o, Rs, ref)
+    phis = [torch.zeros_like(R) for R in Rs]
+    buf = sw.stats_buffer(len(grids))
+    sw.sw_ensemble_solve_async(grids, o, Rs, phis, buf)
+    torch.cuda.synchronize()
+    got = sw.stats_from_device(buf, len(grids))
+    for a, b, p, q in zip(sts, got, ref, phis):
+        assert a.status == b.status == sw.SW_OK
+        assert a.iterations == b.iterations
+        assert a.true_rel_residual == b.true_rel_residual and a.eta == b.eta
+        assert torch.equal(p, q)
+
+
+def test_graph_capture_and_replay():
+    grids, Rs = members()
+    o = sw.sw_solve_opts_default(prec=sw.SW_PREC_MIXED_FP16, tol=1e-8)
+    ref = [torch.zeros_like(R) for R in Rs]
+    sts = sw.sw_ensemble_solve(grids, o, Rs, ref)            # also sizes the workspaces
+    phis = [torch.zeros_like(R) for R in Rs]
+    buf = sw.stats_buffer(len(grids))
+    graph = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(graph, stream=s):
+            for p in phis:
+                p.zero_()
+            sw.sw_ensemble_solve_async(grids, o, Rs, phis, buf)
+    torch.cuda.current_stream().wait_stream(s)
+    for _ in range(2):
+        for p in phis:
+            p.fill_(1.0)                                       # replays start from zero again
+        graph.replay()
+        torch.cuda.synchronize()
+        got = sw.stats_from_device(buf, len(grids))
+        for a, b, p, q in zip(sts, got, ref, phis):
+            assert b.status == sw.SW_OK and a.iterations == b.iterations
+            assert torch.equal(p, q)
+
+
+def test_autotuner_picks_a_width_and_caches_it():
+    grids, Rs = members()
+    o = sw.sw_solve_opts_default(prec=sw.SW_PREC_MIXED_FP16, tol=1e-8)
+    phis = [torch.zeros_like(R) for R in Rs]
+    best, table = autotune.tune_ensemble(grids, o, Rs, phis)
+    assert best.threads_per_row in table and np.isfinite(table[best.threads_per_row])
+    assert all(float(p.abs().max()) == 0.0 for p in phis)     # first guesses restored
+    again, table2 = autotune.tune_ensemble(grids, o, Rs, phis)
+    assert again.threads_per_row == best.threads_per_row and table2 is table
+    sts = sw.sw_ensemble_solve(grids, best, Rs, phis)
+    assert all(s.status == sw.SW_OK and s.true_rel_residual <= 1e-8 for s in sts)
