@@ -30,6 +30,17 @@ struct WgradArgs {
 };
 
 cudaError_t launch_conv(int cin, int cout, bool dgrad, const ConvArgs &a, int sms, cudaStream_t s);
+// the same convolution on tcgen05 (nn_tc.cu) where its rows are a multiple of
+// 128 points and the operands fit in shared memory; err (device) is set if a
+// tensor-core wait ran out
+bool conv_tc_supported(int cin, int cout, bool dgrad, int W);
+cudaError_t launch_conv_tc(int cin, int cout, bool dgrad, const ConvArgs &a, int sms, int *err, cudaStream_t s);
+inline cudaError_t launch_conv_auto(int cin, int cout, bool dgrad, const ConvArgs &a, int sms, int *err,
+                                    cudaStream_t s)
+{
+    return conv_tc_supported(cin, cout, dgrad, a.W) ? launch_conv_tc(cin, cout, dgrad, a, sms, err, s)
+                                                    : launch_conv(cin, cout, dgrad, a, sms, s);
+}
 cudaError_t launch_wgrad(int cin, int cout, const WgradArgs &a, int sms, cudaStream_t s);
 
 // elementwise and small kernels (nn_ops.cu); shapes are of the fine level

@@ -48,6 +48,7 @@ struct sw_model_s {
     float *master, *m, *v, *gflat;
     bf16 *wf[NLAYERS], *wd[NLAYERS];
     float *bias[NLAYERS], *dw[NLAYERS], *db[NLAYERS];
+    int *err;                    // device: a tensor-core wait ran out
     int t = 0;
     Acts A;
 };
@@ -103,6 +104,14 @@ sw_status ensure_acts(sw_model_s *M, int B, int H, int W)
     return SW_OK;
 }
 
+sw_status check_err(sw_model_s *M)
+{
+    int e = 0;
+    NCK(cudaMemcpy(&e, M->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e) return sw::api_fail(SW_ERR_TIMEOUT, "a tensor-core wait of the network ran out");
+    return SW_OK;
+}
+
 ConvArgs conv_args(const bf16 *x, const bf16 *w, const float *bias, bf16 *y, int B, int H, int W, int relu)
 {
     ConvArgs a;
@@ -126,18 +135,18 @@ sw_status forward(sw_model_s *M, int B, int H, int W, const float *x0, cudaStrea
     Acts &A = M->A;
     const int H1 = H / 2, W1 = W / 2, H2 = H / 4, W2 = W / 4;
     NCK(launch_pack_input(x0, A.x0b, B, H, W, s));
-    NCK(launch_conv(16, 32, false, conv_args(A.x0b, M->wf[0], M->bias[0], A.a1, B, H, W, 1), M->sms, s));
+    NCK(launch_conv_auto(16, 32, false, conv_args(A.x0b, M->wf[0], M->bias[0], A.a1, B, H, W, 1), M->sms, M->err, s));
     NCK(launch_pool(A.a1, A.p1, B, H, W, 32, s));
-    NCK(launch_conv(32, 64, false, conv_args(A.p1, M->wf[1], M->bias[1], A.a2, B, H1, W1, 1), M->sms, s));
+    NCK(launch_conv_auto(32, 64, false, conv_args(A.p1, M->wf[1], M->bias[1], A.a2, B, H1, W1, 1), M->sms, M->err, s));
     NCK(launch_pool(A.a2, A.p2, B, H1, W1, 64, s));
-    NCK(launch_conv(64, 64, false, conv_args(A.p2, M->wf[2], M->bias[2], A.a3, B, H2, W2, 1), M->sms, s));
+    NCK(launch_conv_auto(64, 64, false, conv_args(A.p2, M->wf[2], M->bias[2], A.a3, B, H2, W2, 1), M->sms, M->err, s));
     NCK(launch_cat_up(A.a3, 64, A.a2, 64, A.cat4, B, H1, W1, s));
-    NCK(launch_conv(128, 64, false, conv_args(A.cat4, M->wf[3], M->bias[3], A.a4, B, H1, W1, 1), M->sms, s));
+    NCK(launch_conv_auto(128, 64, false, conv_args(A.cat4, M->wf[3], M->bias[3], A.a4, B, H1, W1, 1), M->sms, M->err, s));
     NCK(launch_cat_up(A.a4, 64, A.a1, 32, A.cat5, B, H, W, s));
-    NCK(launch_conv(96, 32, false, conv_args(A.cat5, M->wf[4], M->bias[4], A.a5, B, H, W, 1), M->sms, s));
+    NCK(launch_conv_auto(96, 32, false, conv_args(A.cat5, M->wf[4], M->bias[4], A.a5, B, H, W, 1), M->sms, M->err, s));
     ConvArgs o = conv_args(A.a5, M->wf[5], M->bias[5], nullptr, B, H, W, 0);
     o.yf = A.y; o.yf_c = 1;
-    NCK(launch_conv(32, 16, false, o, M->sms, s));
+    NCK(launch_conv_auto(32, 16, false, o, M->sms, M->err, s));
     return SW_OK;
 }
 
@@ -160,22 +169,22 @@ sw_status backward(sw_model_s *M, int B, int H, int W, const float *target, cuda
     NCK(wg(5, A.gy16, A.a5, B, H, W));
     ConvArgs d6 = conv_args(A.gy16, M->wd[5], nullptr, A.gz5, B, H, W, 0);
     d6.mask = A.a5;
-    NCK(launch_conv(16, 32, true, d6, M->sms, s));
+    NCK(launch_conv_auto(16, 32, true, d6, M->sms, M->err, s));
     // c5 (96 -> 32) on [up(a4), a1]
     NCK(wg(4, A.gz5, A.cat5, B, H, W));
-    NCK(launch_conv(32, 96, true, dgrad_args(A.gz5, M->wd[4], A.gcat5, 96, B, H, W), M->sms, s));
+    NCK(launch_conv_auto(32, 96, true, dgrad_args(A.gz5, M->wd[4], A.gcat5, 96, B, H, W), M->sms, M->err, s));
     NCK(launch_split_up_bwd(A.gcat5, 64, 32, A.a4, A.gz4, A.gskip1, B, H, W, s));
     // c4 (128 -> 64) on [up(a3), a2]
     NCK(wg(3, A.gz4, A.cat4, B, H1, W1));
-    NCK(launch_conv(64, 128, true, dgrad_args(A.gz4, M->wd[3], A.gcat4, 128, B, H1, W1), M->sms, s));
+    NCK(launch_conv_auto(64, 128, true, dgrad_args(A.gz4, M->wd[3], A.gcat4, 128, B, H1, W1), M->sms, M->err, s));
     NCK(launch_split_up_bwd(A.gcat4, 64, 64, A.a3, A.gz3, A.gskip2, B, H1, W1, s));
     // c3 (64 -> 64) on pool(a2)
     NCK(wg(2, A.gz3, A.p2, B, H2, W2));
-    NCK(launch_conv(64, 64, true, dgrad_args(A.gz3, M->wd[2], A.gp2, 64, B, H2, W2), M->sms, s));
+    NCK(launch_conv_auto(64, 64, true, dgrad_args(A.gz3, M->wd[2], A.gp2, 64, B, H2, W2), M->sms, M->err, s));
     NCK(launch_pool_bwd(A.gskip2, A.gp2, A.a2, A.gz2, B, H1, W1, 64, s));
     // c2 (32 -> 64) on pool(a1)
     NCK(wg(1, A.gz2, A.p1, B, H1, W1));
-    NCK(launch_conv(64, 32, true, dgrad_args(A.gz2, M->wd[1], A.gp1, 32, B, H1, W1), M->sms, s));
+    NCK(launch_conv_auto(64, 32, true, dgrad_args(A.gz2, M->wd[1], A.gp1, 32, B, H1, W1), M->sms, M->err, s));
     NCK(launch_pool_bwd(A.gskip1, A.gp1, A.a1, A.gz1, B, H, W, 32, s));
     // c1 (4 -> 32, inputs padded to 16)
     NCK(wg(0, A.gz1, A.x0b, B, H, W));
@@ -318,7 +327,7 @@ extern "C" sw_status sw_model_create(sw_model *out)
     cudaError_t e = cudaGetDevice(&M->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&M->sms, cudaDevAttrMultiProcessorCount, M->device);
     M->np = param_count();
-    size_t bytes = 4 * al256(M->np * 4);
+    size_t bytes = 4 * al256(M->np * 4) + al256(16);
     for (int l = 0; l < NLAYERS; ++l) {
         const size_t nw = (size_t)9 * LAYER[l].cout_pad * LAYER[l].cin_pad;
         bytes += 2 * al256(nw * 2) + al256(nw * 4) + 2 * al256((size_t)LAYER[l].cout_pad * 4);
@@ -334,6 +343,7 @@ extern "C" sw_status sw_model_create(sw_model *out)
     char *p = (char *)M->pmem;
     float **f4[] = {&M->master, &M->m, &M->v, &M->gflat};
     for (auto q : f4) { *q = (float *)p; p += al256(M->np * 4); }
+    M->err = (int *)p; p += al256(16);
     for (int l = 0; l < NLAYERS; ++l) {
         const size_t nw = (size_t)9 * LAYER[l].cout_pad * LAYER[l].cin_pad;
         M->wf[l] = (bf16 *)p; p += al256(nw * 2);
@@ -410,7 +420,7 @@ extern "C" sw_status sw_model_loss_grad(sw_model M, int batch, int ny, int nx, c
     if (loss) NCK(cudaMemcpyAsync(loss, M->A.scal + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
     if (grad) NCK(cudaMemcpyAsync(grad, M->gflat, M->np * 4, cudaMemcpyDeviceToHost, s));
     NCK(cudaStreamSynchronize(s));
-    return SW_OK;
+    return check_err(M);
 }
 
 extern "C" sw_status sw_model_train_step(sw_model M, int batch, int ny, int nx, const float *x0, const float *target,
@@ -432,6 +442,7 @@ extern "C" sw_status sw_model_train_step(sw_model M, int batch, int ny, int nx, 
     if (loss) {
         NCK(cudaMemcpyAsync(loss, M->A.scal + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
         NCK(cudaStreamSynchronize(s));
+        return check_err(M);
     }
     return SW_OK;
 }
