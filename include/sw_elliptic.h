@@ -281,6 +281,16 @@ sw_status sw_model_target(sw_model m, sw_grid g, const float *r, const float *e,
 sw_status sw_gcr_solve_noalloc(sw_grid g, const sw_solve_opts *o, const double *R, double *phi,
                                sw_solve_stats *stats, void *stream);
 
+/* Test hook for failure detection (no counterpart in the paper).  Every
+ * barrier of the solver kernel waits for the arrivals of its member's blocks
+ * for at most a limit (2 s), then stops the solve, which returns
+ * SW_ERR_TIMEOUT with the CUDA context intact.  This call makes later solves
+ * on the current device expect extra_arrivals more arrivals than any block
+ * provides, with a limit of wait_limit_s seconds (0: the default 2 s), so a
+ * test can make that wait run out without any fault.  sw_debug_barrier(0, 0)
+ * restores normal operation. */
+sw_status sw_debug_barrier(int extra_arrivals, double wait_limit_s);
+
 /* Message describing the last error on the calling host thread. */
 const char *sw_last_error(void);
 

@@ -298,3 +298,7 @@ def sw_model_target(m: Model, g: Grid, r, e, y, stream=None) -> None:
     shp = (g.ny, g.nx)
     _check(load().sw_model_target(m.handle, g.handle, _ptr(r, torch.float32, shp), _ptr(e, torch.float32, shp),
                                   _ptr(y, torch.float32, shp), _stream(stream)), "sw_model_target")
+
+
+def sw_debug_barrier(extra_arrivals: int, wait_limit_s: float) -> None:
+    _check(load().sw_debug_barrier(int(extra_arrivals), float(wait_limit_s)), "sw_debug_barrier")

@@ -26,7 +26,7 @@ EXPORTS = (
     "sw_operator_apply", "sw_precond_apply", "sw_gcr_solve", "sw_ensemble_solve", "sw_gcr_solve_noalloc",
     "sw_last_error", "sw_model_create", "sw_model_destroy", "sw_model_set_params", "sw_model_get_params",
     "sw_model_features", "sw_model_forward", "sw_model_loss_grad", "sw_model_train_step", "sw_model_apply",
-    "sw_model_target", "sw_ensemble_solve_async",
+    "sw_model_target", "sw_ensemble_solve_async", "sw_debug_barrier",
 )
 SW_MODEL_PARAMS = 158369
 SW_NOALLOC_SCRATCH_BYTES = 16 << 20
@@ -80,6 +80,7 @@ def load() -> C.CDLL:
     lib.sw_operator_apply.argtypes = [vp, i, vp, vp, vp]
     lib.sw_precond_apply.argtypes = [vp, C.POINTER(SolveOpts), vp, vp, vp]
     lib.sw_gcr_solve.argtypes = [vp, C.POINTER(SolveOpts), vp, vp, C.POINTER(SolveStats), vp]
+    lib.sw_debug_barrier.argtypes = [i, d]
     lib.sw_ensemble_solve_async.argtypes = [i, C.POINTER(vp), C.POINTER(SolveOpts), C.POINTER(vp),
                                             C.POINTER(vp), vp, vp]
     lib.sw_gcr_solve_noalloc.argtypes = [vp, C.POINTER(SolveOpts), vp, vp, C.POINTER(SolveStats), vp]

@@ -828,3 +828,12 @@ extern "C" sw_status sw_ensemble_solve_async(int n, const sw_grid *grids, const 
     if (stats_dev) CK(launch_member_stats(lead->desc, n, stats_dev, s));
     return SW_OK;
 }
+
+extern "C" sw_status sw_debug_barrier(int extra_arrivals, double wait_limit_s)
+{
+    if (extra_arrivals < 0 || !(wait_limit_s >= 0.0) || wait_limit_s > 60.0)
+        return fail(SW_ERR_INVALID_ARG, "sw_debug_barrier: extra_arrivals >= 0, 0 <= wait_limit_s <= 60");
+    const unsigned long long ns = wait_limit_s > 0.0 ? (unsigned long long)(wait_limit_s * 1e9) : 2000000000ull;
+    CK(set_barrier_debug((unsigned long long)extra_arrivals, ns));
+    return SW_OK;
+}

@@ -48,6 +48,7 @@ cudaError_t launch_operator_f32(const OpArgs<float> &a, const float *x, float *y
 cudaError_t launch_precond(int prec, const void *Mdev, int nx, int ny, int nstages, void *qout, int threads,
                            cudaStream_t s);
 cudaError_t launch_fill(double *p, size_t n, double v, cudaStream_t s);
+cudaError_t set_barrier_debug(unsigned long long extra, unsigned long long limit_ns);
 // every member of a launch descriptor: initial GCR state, cleared barrier
 cudaError_t launch_init_members(const EnsDesc *Ddev, int n, cudaStream_t s);
 // every member's sw_solve_stats, written to device memory

@@ -38,7 +38,11 @@
 
 namespace sw {
 
-constexpr unsigned long long WAIT_LIMIT_NS = 2000000000ull;   // longest barrier wait (2 s)
+// longest barrier wait (default 2 s) and arrivals a barrier expects beyond
+// the member's blocks (default 0); sw_debug_barrier changes both, so that a
+// test can make the wait run out
+static __device__ unsigned long long g_wait_limit_ns = 2000000000ull;
+static __device__ unsigned long long g_extra_arrivals = 0;
 
 __device__ __forceinline__ unsigned long long gtimer()
 {
@@ -511,12 +515,13 @@ __global__ void __launch_bounds__(MAX_THREADS) k_gcr(const EnsDesc *__restrict__
         if (threadIdx.x == 0) {
             int okb = 1;
             red_release_add(&G->count, 1ull);
-            const unsigned long long target = (unsigned long long)nb * (unsigned long long)(step + 1);
+            const unsigned long long target = (unsigned long long)nb * (unsigned long long)(step + 1) + g_extra_arrivals;
+            const unsigned long long limit = g_wait_limit_ns;
             if (ld_acquire(&G->count) < target) {
                 const unsigned long long t0 = gtimer();
                 while (ld_acquire(&G->count) < target) {
                     if (vload(&G->abort)) { okb = 0; break; }
-                    if (gtimer() - t0 > WAIT_LIMIT_NS) {
+                    if (gtimer() - t0 > limit) {
                         if (atomicExch(&G->abort, 1) == 0) G->where = step;
                         okb = 0;
                         break;
@@ -828,6 +833,13 @@ extern "C" void sw_trace_configure(unsigned long long *buf, int cap, int block)
     cudaMemcpyToSymbol(g_trace_blk, &block, sizeof(block));
 }
 #endif
+
+cudaError_t set_barrier_debug(unsigned long long extra, unsigned long long limit_ns)
+{
+    cudaError_t e = cudaMemcpyToSymbol(g_extra_arrivals, &extra, sizeof(extra));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_wait_limit_ns, &limit_ns, sizeof(limit_ns));
+    return e;
+}
 
 cudaError_t launch_fill(double *p, size_t n, double v, cudaStream_t s)
 {
