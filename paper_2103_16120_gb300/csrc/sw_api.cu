@@ -449,7 +449,7 @@ extern "C" sw_status sw_precond_apply(sw_grid g, const sw_solve_opts *o, const v
 // linearly with the resolution) and cycle over several rows each, with
 // everything in global memory.
 struct Plan {
-    int grid = 0, cc = 0, cs = 0, threads = 0;
+    int grid = 0, cc = 0, cs = 0, threads = 0, minb = 1;
     size_t smem = 0;
     std::vector<int> nb;
 };
@@ -467,17 +467,21 @@ static sw_status plan_launch(int n, const sw_grid *grids, const sw_solve_opts *o
     for (int lv = (o->pc == SW_PC_LEARNED ? 1 : 0); lv < 3 && !P.grid; ++lv) {
         const size_t sm_l = gcr_smem_bytes(o->prec, max_nx, o->k, levels[lv][0], levels[lv][1]);
         int bps = 0;
-        CK(gcr_occupancy(o->prec, o->k, P.threads, sm_l, &bps));
+        CK(gcr_occupancy(o->prec, o->k, 1, P.threads, sm_l, &bps));
         if (bps > 0 && rows_total <= (long)bps * sms) {
             for (int m = 0; m < n; ++m) P.nb[m] = grids[m]->ny;
             P.grid = (int)rows_total; P.cc = levels[lv][0]; P.cs = levels[lv][1]; P.smem = sm_l;
         }
     }
     if (!P.grid) {
+        // blocks own several rows: take the register budget that fits more
+        // resident blocks
         P.smem = gcr_smem_bytes(o->prec, max_nx, o->k, 0, 0);
         P.cc = P.cs = 0;
-        int bps = 0;
-        CK(gcr_occupancy(o->prec, o->k, P.threads, P.smem, &bps));
+        int bps = 0, bps2 = 0;
+        CK(gcr_occupancy(o->prec, o->k, 1, P.threads, P.smem, &bps));
+        CK(gcr_occupancy(o->prec, o->k, 2, P.threads, P.smem, &bps2));
+        if (bps2 > bps) { bps = bps2; P.minb = 2; }
         if (bps < 1) return fail(SW_ERR_INVALID_ARG, "grid rows too long for the solver kernel");
         const int cap = bps * sms;
         if (n > cap) return fail(SW_ERR_INVALID_ARG, "too many members for one launch on this device");
@@ -590,7 +594,7 @@ static sw_status solve_members(int n, const sw_grid *grids, const sw_solve_opts 
     EnsDesc &D = *lead->h_desc;
     fill_desc(D, n, grids, P);
     CK(cudaMemcpyAsync(lead->desc, &D, sizeof(EnsDesc), cudaMemcpyHostToDevice, s));
-    CK(launch_gcr(o->prec, o->k, lead->desc, grid, max_nx, threads, smem, s));
+    CK(launch_gcr(o->prec, o->k, P.minb, lead->desc, grid, max_nx, threads, smem, s));
     if (o->pc == SW_PC_LEARNED) {
         // flexible GCR: a launch ends where the next direction is the
         // network's; the network runs on r, its output becomes e, and the
@@ -606,7 +610,7 @@ static sw_status solve_members(int n, const sw_grid *grids, const sw_solve_opts 
             if ((st = model_precondition(o->model, g, r, o->prec == SW_PREC_FP64, ef, s))) return st;
             CK(launch_store_e(o->prec, g->blk->dev, ef, g->nx, g->ny, row_threads(g->nx, o->threads_per_row), s));
             CK(cudaMemsetAsync(&g->blk->g, 0, sizeof(GlobalCtl), s));
-            CK(launch_gcr(o->prec, o->k, lead->desc, grid, max_nx, threads, smem, s));
+            CK(launch_gcr(o->prec, o->k, P.minb, lead->desc, grid, max_nx, threads, smem, s));
         }
     }
     for (int m = 0; m < n; ++m) {
@@ -730,7 +734,7 @@ extern "C" sw_status sw_gcr_solve_noalloc(sw_grid g, const sw_solve_opts *o, con
     for (int lv = 0; lv < 3 && !grid; ++lv) {
         const size_t sm_l = gcr_smem_bytes(o->prec, g->nx, o->k, levels[lv][0], levels[lv][1]);
         int bps = 0;
-        CK(gcr_occupancy(o->prec, o->k, threads, sm_l, &bps));
+        CK(gcr_occupancy(o->prec, o->k, 1, threads, sm_l, &bps));
         if (bps > 0 && g->ny <= bps * g->sms) {
             grid = g->ny; cc = levels[lv][0]; cs = levels[lv][1]; smem = sm_l;
         }
@@ -738,7 +742,7 @@ extern "C" sw_status sw_gcr_solve_noalloc(sw_grid g, const sw_solve_opts *o, con
     if (!grid) {
         smem = gcr_smem_bytes(o->prec, g->nx, o->k, 0, 0);
         int bps = 0;
-        CK(gcr_occupancy(o->prec, o->k, threads, smem, &bps));
+        CK(gcr_occupancy(o->prec, o->k, 1, threads, smem, &bps));
         if (bps < 1) return fail(SW_ERR_INVALID_ARG, "sw_gcr_solve_noalloc: grid rows too long for the solver kernel");
         grid = std::min(bps * g->sms, g->ny);
     }
@@ -751,7 +755,7 @@ extern "C" sw_status sw_gcr_solve_noalloc(sw_grid g, const sw_solve_opts *o, con
     D.cta_begin[1] = grid;
     D.blk[0] = g->blk;
     CK(cudaMemcpyAsync(g->desc, &D, sizeof(EnsDesc), cudaMemcpyHostToDevice, s));
-    CK(launch_gcr(o->prec, o->k, g->desc, grid, g->nx, threads, smem, s));
+    CK(launch_gcr(o->prec, o->k, 1, g->desc, grid, g->nx, threads, smem, s));
     CK(cudaMemcpyAsync(g->h_ctl, &g->blk->ctl, sizeof(MemberCtl) + sizeof(GlobalCtl), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(g->h_eta, g->eta, sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -824,7 +828,7 @@ extern "C" sw_status sw_ensemble_solve_async(int n, const sw_grid *grids, const 
     fill_desc(*lead->h_desc, n, grids, P);
     CK(cudaMemcpyAsync(lead->desc, lead->h_desc, sizeof(EnsDesc), cudaMemcpyHostToDevice, s));
     CK(launch_init_members(lead->desc, n, s));
-    CK(launch_gcr(o->prec, o->k, lead->desc, P.grid, max_nx, P.threads, P.smem, s));
+    CK(launch_gcr(o->prec, o->k, P.minb, lead->desc, P.grid, max_nx, P.threads, P.smem, s));
     if (stats_dev) CK(launch_member_stats(lead->desc, n, stats_dev, s));
     return SW_OK;
 }

@@ -40,9 +40,9 @@ struct FactorArgs {
 cudaError_t launch_faces(const FaceArgs &a, int threads, cudaStream_t s);
 cudaError_t launch_factor(const FactorArgs &a, int threads, cudaStream_t s);
 size_t gcr_smem_bytes(int prec, int max_nx, int k, int cache_const, int cache_state);
-cudaError_t gcr_occupancy(int prec, int k, int threads, size_t smem, int *blocks_per_sm);
-cudaError_t launch_gcr(int prec, int k, const EnsDesc *Ddev, int grid, int max_nx, int threads, size_t smem,
-                       cudaStream_t s);
+cudaError_t gcr_occupancy(int prec, int k, int minb, int threads, size_t smem, int *blocks_per_sm);
+cudaError_t launch_gcr(int prec, int k, int minb, const EnsDesc *Ddev, int grid, int max_nx, int threads,
+                       size_t smem, cudaStream_t s);
 cudaError_t launch_operator_f64(const OpArgs<double> &a, const double *x, double *y, int threads, cudaStream_t s);
 cudaError_t launch_operator_f32(const OpArgs<float> &a, const float *x, float *y, int threads, cudaStream_t s);
 cudaError_t launch_precond(int prec, const void *Mdev, int nx, int ny, int nstages, void *qout, int threads,

@@ -423,9 +423,12 @@ __device__ void advance(const MemberDev<Pol> &M, MemberCtl &c, const typename Ac
 // the persistent GCR kernel
 // ---------------------------------------------------------------------------
 // KM: directions a cycle can hold (k <= KM); it sizes the per-thread
-// registers of the inner-product and update loops
-template <class Pol, int KM>
-__global__ void __launch_bounds__(MAX_THREADS) k_gcr(const EnsDesc *__restrict__ D, int max_nx)
+// registers of the inner-product and update loops.  MINB: resident blocks
+// per SM the register allocation is made for (2 for grids whose blocks own
+// several rows each: twice the warps to overlap their memory latency, at the
+// price of a few spilled registers)
+template <class Pol, int KM, int MINB>
+__global__ void __launch_bounds__(MAX_THREADS, MINB) k_gcr(const EnsDesc *__restrict__ D, int max_nx)
 {
     typedef typename Pol::comp comp;
     typedef typename Acc<Pol>::type acc_t;
@@ -675,21 +678,27 @@ size_t gcr_smem_bytes(int prec, int max_nx, int k, int cache_const, int cache_st
     }
 }
 
-// the instantiation of k_gcr for a precision and a GCR k
-static const void *gcr_kernel(int prec, int k)
+// the instantiation of k_gcr for a precision, a GCR k and the register budget
+template <class Pol>
+static const void *gcr_kernel_t(int k, int minb)
 {
-    const bool small = k <= 4;
+    if (k <= 4) return minb > 1 ? (const void *)k_gcr<Pol, 4, 2> : (const void *)k_gcr<Pol, 4, 1>;
+    return minb > 1 ? (const void *)k_gcr<Pol, KMAX, 2> : (const void *)k_gcr<Pol, KMAX, 1>;
+}
+
+static const void *gcr_kernel(int prec, int k, int minb)
+{
     switch (prec) {
-    case 0: return small ? (const void *)k_gcr<PolFP64, 4> : (const void *)k_gcr<PolFP64, KMAX>;
-    case 1: return small ? (const void *)k_gcr<PolF16, 4> : (const void *)k_gcr<PolF16, KMAX>;
-    case 2: return small ? (const void *)k_gcr<PolBF16, 4> : (const void *)k_gcr<PolBF16, KMAX>;
+    case 0: return gcr_kernel_t<PolFP64>(k, minb);
+    case 1: return gcr_kernel_t<PolF16>(k, minb);
+    case 2: return gcr_kernel_t<PolBF16>(k, minb);
     default: return nullptr;
     }
 }
 
-cudaError_t gcr_occupancy(int prec, int k, int threads, size_t smem, int *blocks_per_sm)
+cudaError_t gcr_occupancy(int prec, int k, int minb, int threads, size_t smem, int *blocks_per_sm)
 {
-    const void *f = gcr_kernel(prec, k);
+    const void *f = gcr_kernel(prec, k, minb);
     if (!f) return cudaErrorInvalidValue;
     if (smem > 227 * 1024 - 8192) { *blocks_per_sm = 0; return cudaSuccess; }
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -697,10 +706,10 @@ cudaError_t gcr_occupancy(int prec, int k, int threads, size_t smem, int *blocks
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, threads, smem);
 }
 
-cudaError_t launch_gcr(int prec, int k, const EnsDesc *Ddev, int grid, int max_nx, int threads, size_t smem,
-                       cudaStream_t s)
+cudaError_t launch_gcr(int prec, int k, int minb, const EnsDesc *Ddev, int grid, int max_nx, int threads,
+                       size_t smem, cudaStream_t s)
 {
-    const void *f = gcr_kernel(prec, k);
+    const void *f = gcr_kernel(prec, k, minb);
     if (!f) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
