@@ -1,0 +1,84 @@
+"""Full-size checks in the launch configurations the benchmark times.
+
+The oracle recomputes, in FP64 and with its own operator, the residual
+||L(Phi) - R|| / ||R|| of the GPU's solutions:
+* the 2048 x 1024 problem (config 4), mixed FP16;
+* all 64 members of the ensemble (config 2), solved in one launch;
+* the first steps of the 512 x 256 warm-started sequence (config 1), whose
+  solution is also compared with the oracle's own GCR solution.
+
+The GPU's exit test uses its FP64 true residual at tol = 1e-8.  The oracle
+recomputes the same quantity in another summation order, so the bar is
+1.001 * tol.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2103_16120_gb300 as sw  # noqa: E402
+
+TOL = 1e-8
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _build():
+    from paper_2103_16120_gb300 import build
+    build.build()
+    assert torch.cuda.is_available()
+
+
+def grid_for(P):
+    ny, nx = P["C"].shape
+    g = sw.sw_grid_create(nx, ny)
+    sw.sw_elliptic_set_coeffs(g, *[torch.as_tensor(P[k], device="cuda") for k in sw.COEFF_KEYS])
+    return g
+
+
+def oracle_rel_residual(P, phi):
+    r = O.Problem(P).operator(phi) - P["R"]
+    return float(np.linalg.norm(r) / np.linalg.norm(P["R"]))
+
+
+def test_large_2048x1024_mixed():
+    P = synth.sequence_problem(2048, 1024, 4000, 0)
+    g = grid_for(P)
+    R = torch.as_tensor(P["R"], device="cuda")
+    phi = torch.zeros_like(R)
+    st = sw.sw_gcr_solve(g, sw.sw_solve_opts_default(prec=sw.SW_PREC_MIXED_FP16, tol=TOL, max_iters=4000), R, phi)
+    assert st.status == sw.SW_OK and st.true_rel_residual <= TOL
+    assert oracle_rel_residual(P, phi.cpu().numpy()) <= 1.001 * TOL
+
+
+def test_ensemble_64_members():
+    members = synth.ensemble_members()
+    Ps = [synth.problem(nx, ny, seed) for nx, ny, seed in members]
+    grids = [grid_for(P) for P in Ps]
+    Rs = [torch.as_tensor(P["R"], device="cuda") for P in Ps]
+    phis = [torch.zeros_like(R) for R in Rs]
+    sts = sw.sw_ensemble_solve(grids, sw.sw_solve_opts_default(prec=sw.SW_PREC_MIXED_FP16, tol=TOL), Rs, phis)
+    for P, st, phi in zip(Ps, sts, phis):
+        assert st.status == sw.SW_OK
+        assert oracle_rel_residual(P, phi.cpu().numpy()) <= 1.001 * TOL
+
+
+def test_sequence_512x256_warm_start():
+    g = None
+    phi = torch.zeros((256, 512), dtype=torch.float64, device="cuda")
+    o = sw.sw_solve_opts_default(k=4, prec=sw.SW_PREC_MIXED_FP16, tol=TOL, max_iters=2000)
+    for t in range(3):
+        P = synth.sequence_problem(512, 256, 1000, t)
+        if g is None:
+            g = grid_for(P)
+        else:
+            sw.sw_elliptic_set_coeffs(g, *[torch.as_tensor(P[k], device="cuda") for k in sw.COEFF_KEYS])
+        st = sw.sw_gcr_solve(g, o, torch.as_tensor(P["R"], device="cuda"), phi)
+        assert st.status == sw.SW_OK
+        x = phi.cpu().numpy()
+        assert oracle_rel_residual(P, x) <= 1.001 * TOL
+    ref, _ = O.Problem(P).gcr(P["R"], O.Opts(k=4, tol=1e-13, max_iters=5000))
+    assert np.linalg.norm(x - ref) <= 1e-6 * np.linalg.norm(ref)
