@@ -49,6 +49,8 @@ import synth  # noqa: E402
 METRIC = "elliptic solves/s at 1e-8 rel. residual: mixed+learned vs FP64 GCR, same GB300"
 NX, NY, NSEQ, SEED, TOL, K_GCR = 512, 256, 200, 1000, 1e-8, 4
 WORKLOAD = "sequence of 200 solves, 512x256 lon/lat grid, evolving coefficients, warm start"
+# DRAM bytes of one mixed-precision solve launch of this workload, measured with ncu
+TRAFFIC_512 = 15411968 + 5376
 KEYS = ("A11", "A12", "A21", "A22", "B1", "B2", "C")
 
 
@@ -347,7 +349,9 @@ def run_gpu(args):
             "mean_iterations": its_m,
             "solution_rel_error_vs_fp64_oracle": err,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak, "traffic": TRAFFIC_512,
+                         "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch, "
+                                           "profiles/k_gcr_f16_seq512x256.md",
                          "kernel": "k_gcr<PolF16> (persistent GCR)",
                          "note": "algorithmic bytes of one solve / solver time; working set is L2-resident "
                                  "and the solve is grid-barrier-latency bound at this size",
