@@ -637,7 +637,7 @@ static sw_status solve_members(int n, const sw_grid *grids, const sw_solve_opts 
             S.r0_norm = c.r0;
             S.R_norm = c.nR;
             S.true_rel_residual = c.nR > 0 ? c.rn_true / c.nR : 0.0;
-            S.recursive_rel_residual = c.nR > 0 ? c.rn_rec / c.nR : 0.0;
+            S.recursive_rel_residual = c.nR > 0 ? std::sqrt(c.rn2_rec) / c.nR : 0.0;
             S.eta = *g->h_eta;
         }
         if (mst != SW_OK && first == SW_OK) first = (sw_status)mst;
@@ -771,7 +771,7 @@ extern "C" sw_status sw_gcr_solve_noalloc(sw_grid g, const sw_solve_opts *o, con
         stats->r0_norm = r.r0;
         stats->R_norm = r.nR;
         stats->true_rel_residual = r.nR > 0 ? r.rn_true / r.nR : 0.0;
-        stats->recursive_rel_residual = r.nR > 0 ? r.rn_rec / r.nR : 0.0;
+        stats->recursive_rel_residual = r.nR > 0 ? std::sqrt(r.rn2_rec) / r.nR : 0.0;
         stats->eta = *g->h_eta;
     }
     switch (mst) {

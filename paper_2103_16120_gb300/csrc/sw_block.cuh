@@ -66,10 +66,10 @@ __device__ __forceinline__ T warp_sum32(T (&v)[32])
 }
 
 // Block sum of NV <= 32 values per thread; tot[q] (shared memory) receives
-// total q.  scratch: 32 values per warp.  Fixed order: a warp butterfly, then
-// the warps in index order.
+// total q in FP64.  scratch: 32 doubles per warp.  Fixed order: a warp
+// butterfly in T, then the warps in index order in FP64.
 template <int NV, class T>
-__device__ __forceinline__ void block_sum_many(const T (&x)[NV], T *tot, T *scratch)
+__device__ __forceinline__ void block_sum_many(const T (&x)[NV], double *tot, double *scratch)
 {
     static_assert(NV <= 32, "");
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -77,10 +77,10 @@ __device__ __forceinline__ void block_sum_many(const T (&x)[NV], T *tot, T *scra
 #pragma unroll
     for (int q = 0; q < 32; ++q) v[q] = q < NV ? x[q] : T(0);
     const T s = warp_sum32(v);
-    scratch[w * 32 + lane] = s;
+    scratch[w * 32 + lane] = (double)s;
     __syncthreads();
     if (threadIdx.x < NV) {
-        T t = 0;
+        double t = 0;
         for (int ww = 0; ww < nw; ++ww) t += scratch[ww * 32 + threadIdx.x];
         tot[threadIdx.x] = t;
     }

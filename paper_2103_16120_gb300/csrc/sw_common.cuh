@@ -59,8 +59,10 @@ struct PolBF16 {
     static constexpr bool kMixed = true;
 };
 
-// accumulation type of the inner products within a warp: FP64 for the FP64
-// policy; FP32 for the mixed policies (block and member sums are FP64)
+// accumulation type of each thread's inner-product partials and of the warp
+// sums: FP64 for the FP64 policy, FP32 for the mixed policies (at most 32
+// threads' partials of a few products each).  The block sums over warps, the
+// member sums over blocks and the GCR scalars are FP64 for every policy.
 template <class Pol> struct Acc { typedef double type; };
 template <> struct Acc<PolF16> { typedef float type; };
 template <> struct Acc<PolBF16> { typedef float type; };
@@ -121,11 +123,13 @@ struct MemberCtl {
     int phase, stage, it, nu, base, init, status, pad_;
     int fb_now, fallbacks;          // learned preconditioner: this iteration fell back; count
     int net_turn, pad2_;            // learned preconditioner: the next direction is the network's
-    double beta, nR, r0, rn_rec, rn_true;
-    double rn_cur;                  // ||r|| of the residual the next direction works on
+    double beta, nR, r0, rn_true;
+    double rn2_rec;                 // ||r||^2 of the recursive residual
+    double rn2_cur;                 // ||r||^2 of the residual the next direction works on
     double g3;                      // share of ||r||^2 the last option-3 direction removed
     double alpha[KMAX + 1];
     double G[KMAX + 1][KMAX + 1];   // Gram matrix <L p_l, L p_m> of the cycle (logical)
+    double Ginv[KMAX + 1];          // 1 / G[l][l], formed once per direction
 };
 
 struct GlobalCtl {

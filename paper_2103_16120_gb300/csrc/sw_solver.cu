@@ -53,6 +53,30 @@ __device__ __forceinline__ unsigned long long gtimer()
 
 __device__ __forceinline__ int vload(const int *p) { return *(const volatile int *)p; }
 
+// Double-float arithmetic (a value as an unevaluated sum hi + lo of two
+// floats; Knuth's error-free TwoSum), for the member-wide sums: about 44
+// significant bits on the FP32 pipe, which on this GPU is 64 times faster
+// than FP64.  Every block adds in the same order, so all agree bit for bit.
+struct dfloat {
+    float hi, lo;
+};
+
+__device__ __forceinline__ dfloat df_split(double x)
+{
+    const float h = (float)x;
+    return dfloat{h, (float)(x - (double)h)};
+}
+
+__device__ __forceinline__ dfloat df_add(dfloat a, dfloat b)
+{
+    const float s = a.hi + b.hi;
+    const float v = s - a.hi;
+    float e = (a.hi - (s - v)) + (b.hi - v);
+    e += a.lo + b.lo;
+    const float hi = s + e;
+    return dfloat{hi, e - (hi - s)};
+}
+
 template <class Pol>
 __device__ __forceinline__ const MemberDev<Pol> *mdev(SolverBlock *b) { return (const MemberDev<Pol> *)b->dev; }
 
@@ -299,18 +323,19 @@ __device__ void phase_prec0(const MemberDev<Pol> &M, const RowView<Pol> &v, type
 }
 
 // ---------------------------------------------------------------------------
-// state transition after a phase, from the member-wide sums tot[slot].  The
-// scalars (alpha, beta, the Gram update, norms) are computed in the policy's
-// accumulation type: FP64 for the FP64 policy, FP32 for the mixed policies,
-// whose vectors are FP32 anyway; the state keeps them in FP64.
+// state transition after a phase, from the member-wide FP64 sums tot[slot].
+// The scalars (alpha, beta, the Gram update, norms) are FP64 for every policy.
+// (The text's half-precision variant keeps these global sums in single
+// precision, Sec. 4.3.)
 // ---------------------------------------------------------------------------
 template <class Pol>
-__device__ void advance(const MemberDev<Pol> &M, MemberCtl &c, const typename Acc<Pol>::type *tot, bool writer)
+__device__ void advance(const MemberDev<Pol> &M, MemberCtl &c, const double *tot, bool writer)
 {
-    typedef typename Acc<Pol>::type sc;
+    typedef double sc;
     const int k = M.k, nd = c.nu + 1;
-    // the mixed policies sum the norms in FP32 (relative error < 1e-6): their
-    // exit test keeps that margin below the tolerance
+    // the mixed policies sum a warp's products in FP32 before the FP64 sums
+    // (relative error < 1e-6): their exit test keeps that margin below the
+    // tolerance
     const double tolR = M.tol * c.nR * (Pol::kMixed ? (1.0 - 1e-5) : 1.0);
     bool done = false;
     // the learned preconditioner alternates its directions with option 3's:
@@ -330,7 +355,8 @@ __device__ void advance(const MemberDev<Pol> &M, MemberCtl &c, const typename Ac
             c.init = 0;
             c.nR = sqrt((double)tot[S_B]);
             c.r0 = rn;
-            c.rn_true = c.rn_rec = c.rn_cur = rn;
+            c.rn_true = rn;
+            c.rn2_rec = c.rn2_cur = (double)tot[S_A];
             c.nu = -1;
             if (writer && M.hist) M.hist[0] = c.nR > 0.0 ? rn / c.nR : 0.0;
             if (c.nR == 0.0) { c.phase = PH_ZERO; break; }
@@ -338,7 +364,8 @@ __device__ void advance(const MemberDev<Pol> &M, MemberCtl &c, const typename Ac
             if (rn <= M.tol * c.nR * (Pol::kMixed ? (1.0 - 1e-5) : 1.0) && M.min_iters <= 0) { finish(ST_OK); break; }
             to_precond();
         } else {
-            c.rn_true = c.rn_cur = rn;
+            c.rn_true = rn;
+            c.rn2_cur = (double)tot[S_A];
             if (writer && M.hist) M.hist[c.it] = rn / c.nR;
             if (!isfinite(rn)) { finish(ST_NONFINITE); break; }
             if (rn <= tolR && c.it >= M.min_iters) { finish(ST_OK); break; }
@@ -359,7 +386,7 @@ __device__ void advance(const MemberDev<Pol> &M, MemberCtl &c, const typename Ac
         // alpha_l of the text; <Lp_new, Lp_new> and <r, Lp_new> of the
         // direction Lp_new = Le + sum alpha_l Lp_l, from the Gram matrix
         sc a[KMAX], lplp = tot[S_A], rlp = tot[S_B];
-        for (int l = 0; l < nd; ++l) a[l] = -tot[S_C0 + l] / (sc)c.G[l][l];
+        for (int l = 0; l < nd; ++l) a[l] = -tot[S_C0 + l] * (sc)c.Ginv[l];
         for (int l = 0; l < nd; ++l) {
             sc rowv = (sc)2 * tot[S_C0 + l];
             for (int m = 0; m < nd; ++m) rowv += a[m] * (sc)c.G[l][m];
@@ -371,7 +398,7 @@ __device__ void advance(const MemberDev<Pol> &M, MemberCtl &c, const typename Ac
             // the network's direction would remove rlp^2 / lplp of ||r||^2; it
             // must remove at least fb_ratio times the share the last option-3
             // direction removed, else this iteration takes option 3
-            const double gain = (double)rlp * (double)rlp / ((double)lplp * c.rn_cur * c.rn_cur);
+            const double gain = (double)rlp * (double)rlp / ((double)lplp * c.rn2_cur);
             if (!(lplp > sc(0)) || !isfinite(lplp) || !isfinite(rlp) || !(gain >= M.fb_ratio * c.g3)) {
                 c.fb_now = 1;
                 c.fallbacks += 1;
@@ -387,23 +414,26 @@ __device__ void advance(const MemberDev<Pol> &M, MemberCtl &c, const typename Ac
     case PH_UB: {
         const int ln = nd;                        // logical index of the new direction
         c.it += 1;
-        const double rn = sqrt((double)tot[S_A]);
-        if (learned && (!c.net_turn || c.fb_now) && c.rn_cur > 0.0)
-            c.g3 = 1.0 - (rn / c.rn_cur) * (rn / c.rn_cur);      // an option-3 direction
-        c.rn_rec = c.rn_cur = rn;
+        // squared norms: no square root on the path of every iteration
+        const double rn2 = (double)tot[S_A];
+        if (learned && (!c.net_turn || c.fb_now) && c.rn2_cur > 0.0)
+            c.g3 = 1.0 - rn2 / c.rn2_cur;                           // an option-3 direction
+        c.rn2_rec = c.rn2_cur = rn2;
         c.fb_now = 0;
         if (learned) c.net_turn ^= 1;
-        if (writer && M.hist) M.hist[c.it] = rn / c.nR;
+        if (writer && M.hist) M.hist[c.it] = sqrt(rn2) / c.nR;
         c.G[ln][ln] = (double)tot[S_B];
+        c.Ginv[ln] = 1.0 / c.G[ln][ln];
         for (int m = 0; m < ln; ++m) c.G[ln][m] = c.G[m][ln] = (double)tot[S_C0 + m];
         c.nu = ln;
         if (c.nu == k) {                          // restart: p_0 <- p_k
             c.base = phys_slot(c, k, k);
             c.G[0][0] = c.G[k][k];
+            c.Ginv[0] = c.Ginv[k];
             c.nu = 0;
         }
-        if (!isfinite(rn)) { finish(ST_NONFINITE); break; }
-        if ((rn <= tolR && c.it >= M.min_iters) || (M.ru_every > 0 && c.it % M.ru_every == 0) ||
+        if (!isfinite(rn2)) { finish(ST_NONFINITE); break; }
+        if ((rn2 <= tolR * tolR && c.it >= M.min_iters) || (M.ru_every > 0 && c.it % M.ru_every == 0) ||
             c.it >= M.max_iters)
             c.phase = PH_TRUE;
         else
@@ -411,7 +441,7 @@ __device__ void advance(const MemberDev<Pol> &M, MemberCtl &c, const typename Ac
         break;
     }
     case PH_ZERO:
-        c.rn_true = c.rn_rec = 0.0;
+        c.rn_true = c.rn2_rec = 0.0;
         finish(ST_OK);
         break;
     default: break;
@@ -436,8 +466,8 @@ __global__ void __launch_bounds__(MAX_THREADS, MINB) k_gcr(const EnsDesc *__rest
     __shared__ MemberDev<Pol> s_M;
     __shared__ MemberCtl s_c;
     __shared__ int s_m, s_ok;
-    __shared__ acc_t s_blk[32];
-    __shared__ acc_t s_tot[NSLOT];
+    __shared__ double s_blk[32];
+    __shared__ double s_tot[NSLOT];
     if (threadIdx.x == 0) {
         int lo = 0, hi = D->n;
         while (hi - lo > 1) {
@@ -461,7 +491,7 @@ __global__ void __launch_bounds__(MAX_THREADS, MINB) k_gcr(const EnsDesc *__rest
     const MemberDev<Pol> &M = s_M;
     const int ny = M.ny, nx = M.nx;
     unsigned char *ws = dsm;
-    acc_t *scratch = (acc_t *)(ws + red_offset<Pol>(nx));
+    double *scratch = (double *)(ws + red_offset<Pol>(nx));
     unsigned char *cslot = dsm + work_bytes<Pol>(max_nx);
     unsigned char *sslot = cslot + (D->cache_const ? const_bytes<Pol>(max_nx) : 0);
     // this block's rows: j = local + t * nb; the first one may be cached
@@ -475,7 +505,7 @@ __global__ void __launch_bounds__(MAX_THREADS, MINB) k_gcr(const EnsDesc *__rest
     __syncthreads();
     const comp eta = (comp)(*M.etap);
     GlobalCtl *G = &B->g;
-    acc_t *partg = (acc_t *)M.part;
+    double *partg = M.part;
     bool ok = true;
     int par = 0;
     for (int step = 0; s_c.phase != PH_DONE && s_c.phase != PH_EXT; ++step) {
@@ -504,12 +534,14 @@ __global__ void __launch_bounds__(MAX_THREADS, MINB) k_gcr(const EnsDesc *__rest
         // block sums of the partials, published slot-major
         int slot[NSLOT];
         const int ns = phase_slots(s_c.phase, s_c.nu + 1, slot);
-        acc_t *pbuf = partg + (size_t)par * NSLOT * ny;
+        double *pbuf = partg + (size_t)par * NSLOT * ny;
         if (ns > 0) {
             block_sum_many<NP, acc_t>(part, s_blk, scratch);
             if (threadIdx.x < ns) {
                 const int g = slot[threadIdx.x];          // slot of tot; its place in part
-                pbuf[(size_t)threadIdx.x * ny + local] = s_blk[g < S_T0 ? g : g - S_T0 + 2 + KM];
+                const double bs = s_blk[g < S_T0 ? g : g - S_T0 + 2 + KM];
+                if constexpr (Pol::kMixed) ((dfloat *)pbuf)[(size_t)threadIdx.x * ny + local] = df_split(bs);
+                else pbuf[(size_t)threadIdx.x * ny + local] = bs;
             }
         }
         __syncthreads();
@@ -538,17 +570,34 @@ __global__ void __launch_bounds__(MAX_THREADS, MINB) k_gcr(const EnsDesc *__rest
         if (!s_ok) { ok = false; break; }
         SW_TRACE(32);
         // member-wide sums, every block in the same order: warp w adds slots
-        // w, w + nwarps, ... over the member's blocks
+        // w, w + nwarps, ... over the member's blocks, in FP64 (FP64 policy)
+        // or in double-float arithmetic (mixed policies, whose magnitudes
+        // stay far inside the FP32 range)
         if (ns > 0) {
             const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
             for (int q = w; q < ns; q += nw) {
-                const acc_t *src = pbuf + (size_t)q * ny;
-                acc_t t = 0;
+                if constexpr (Pol::kMixed) {
+                    const float2 *src = (const float2 *)pbuf + (size_t)q * ny;
+                    dfloat t{0.f, 0.f};
 #pragma unroll 8
-                for (int b = lane; b < nb; b += 32) t += __ldcg(src + b);
+                    for (int b = lane; b < nb; b += 32) {
+                        const float2 x = __ldcg(src + b);
+                        t = df_add(t, dfloat{x.x, x.y});
+                    }
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-                if (lane == 0) s_tot[slot[q]] = t;
+                    for (int o = 16; o > 0; o >>= 1)
+                        t = df_add(t, dfloat{__shfl_xor_sync(0xffffffffu, t.hi, o),
+                                             __shfl_xor_sync(0xffffffffu, t.lo, o)});
+                    if (lane == 0) s_tot[slot[q]] = (double)t.hi + (double)t.lo;
+                } else {
+                    const double *src = pbuf + (size_t)q * ny;
+                    double t = 0;
+#pragma unroll 8
+                    for (int b = lane; b < nb; b += 32) t += __ldcg(src + b);
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+                    if (lane == 0) s_tot[slot[q]] = t;
+                }
             }
         }
         __syncthreads();
@@ -571,8 +620,8 @@ __global__ void __launch_bounds__(MAX_THREADS, MINB) k_gcr(const EnsDesc *__rest
             if (s_c.nR > 0.0)
                 for (int i = threadIdx.x; i < nx; i += blockDim.x) { double x = (double)r[i]; t += x * x; }
             double tv[1] = {t};
-            block_sum_many<1, double>(tv, (double *)s_blk, (double *)scratch);
-            if (threadIdx.x == 0) M.rowres[j] = sqrt(((double *)s_blk)[0]);
+            block_sum_many<1, double>(tv, s_blk, scratch);
+            if (threadIdx.x == 0) M.rowres[j] = sqrt(s_blk[0]);
             __syncthreads();
         }
     }
@@ -814,7 +863,7 @@ __global__ void k_member_stats(const EnsDesc *D, sw_solve_stats *out)
     S.r0_norm = c.r0;
     S.R_norm = c.nR;
     S.true_rel_residual = c.nR > 0 ? c.rn_true / c.nR : 0.0;
-    S.recursive_rel_residual = c.nR > 0 ? c.rn_rec / c.nR : 0.0;
+    S.recursive_rel_residual = c.nR > 0 ? sqrt(c.rn2_rec) / c.nR : 0.0;
     S.eta = *M->etap;
     out[m] = S;
 }
