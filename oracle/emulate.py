@@ -183,3 +183,94 @@ class MixedSolve:
                 p, Lp, nu = [p[k]], [Lp[k]], 0
         st["iterations"] = it
         return phi, st
+
+
+# ---------------------------------------------------------------------------
+# Split fluid thickness for the residual (Sec. 4.2, Eq. 14)
+# ---------------------------------------------------------------------------
+# The paper computes r0 = L(Phi) - R in single precision with Phi held as two
+# single-precision fields, Phi ~ Phi_hat + Phi_tilde: Phi_hat is the depth
+# truncated at a refresh (every 100 steps), Phi_tilde the truncated remainder,
+# to which the solver's increments are added.  In Eq. 14 the derivatives of
+# Phi_hat are computed once per refresh and stored; those of Phi_tilde, their
+# sums, the B and C terms on Phi_SP = Phi_hat + Phi_tilde and the divergence
+# run in single precision.
+#
+# operator_np evaluates the flux form of L (the oracle's stencil, Eq. 10) in
+# the arithmetic of `dtype` with numpy, whose float32 operations are IEEE
+# single precision with rounding to nearest (one rounding per operation, no
+# fused multiply-add).  With `hat` given, x is Phi_tilde and the derivative
+# parts of Phi_hat come from face_gradients(hat).
+
+def _ghost(x, dj):
+    """Rows j + dj for every row j: beyond a pole, the pole row shifted by half
+    a circle (the across-pole continuation of the stencil)."""
+    ny, nx = x.shape
+    out = np.empty_like(x)
+    for j in range(ny):
+        jj = j + dj
+        if jj < 0:
+            out[j] = np.roll(x[0], -(nx // 2))
+        elif jj >= ny:
+            out[j] = np.roll(x[ny - 1], -(nx // 2))
+        else:
+            out[j] = x[jj]
+    return out
+
+
+def face_gradients(x, dtype=np.float64):
+    """The four derivative parts of the face fluxes of x, in dtype:
+    gxl = d/dlam and gxp = d/dphi on the zonal faces (i+1/2, j), gyp = d/dphi
+    and gyl = d/dlam on the meridional faces (i, j+1/2)."""
+    x = np.asarray(x, dtype=dtype)
+    ny, nx = x.shape
+    dlam, dphi = dtype(2.0 * np.pi / nx), dtype(np.pi / ny)
+    e = np.roll(x, -1, axis=1)                       # x[i+1, j]
+    n, s = _ghost(x, 1), _ghost(x, -1)               # x[i, j+1], x[i, j-1]
+    gxl = (e - x) / dlam
+    gxp = ((n + np.roll(n, -1, axis=1)) - (s + np.roll(s, -1, axis=1))) / (dtype(4.0) * dphi)
+    gyp = (n - x) / dphi
+    gyl = ((e + np.roll(n, -1, axis=1)) - (np.roll(x, 1, axis=1) + np.roll(n, 1, axis=1))) / (dtype(4.0) * dlam)
+    return gxl, gxp, gyp, gyl
+
+
+def operator_np(coeffs: dict, x, dtype=np.float64, hat=None, hat_grads=None):
+    """L(x) of Eq. 10 in dtype arithmetic; with hat (and its stored gradients
+    hat_grads), L(hat + x) by Eq. 14: derivatives as stored ones of hat plus
+    those of x, the B and C terms on the dtype sum hat + x."""
+    x = np.asarray(x, dtype=dtype)
+    ny, nx = x.shape
+    dlam, dphi = dtype(2.0 * np.pi / nx), dtype(np.pi / ny)
+    half = dtype(0.5)
+
+    def xmean(c):                                    # face means, rounded to dtype
+        return (0.5 * (c + np.roll(c, -1, axis=1))).astype(dtype)
+
+    def ymean(c):
+        m = np.zeros_like(c)
+        m[:-1] = 0.5 * (c[:-1] + c[1:])
+        return m.astype(dtype)
+
+    a11, a12, b1 = (xmean(coeffs[k]) for k in ("A11", "A12", "B1"))
+    a22, a21, b2 = (ymean(coeffs[k]) for k in ("A22", "A21", "B2"))
+    C = np.asarray(coeffs["C"]).astype(dtype)
+    gxl, gxp, gyp, gyl = face_gradients(x, dtype)
+    sp = x
+    if hat is not None:
+        h = [np.asarray(g).astype(dtype) for g in hat_grads]
+        gxl, gxp, gyp, gyl = gxl + h[0], gxp + h[1], gyp + h[2], gyl + h[3]
+        sp = np.asarray(hat, dtype=dtype) + x
+    fx = a11 * gxl + a12 * gxp + b1 * (half * (sp + np.roll(sp, -1, axis=1)))
+    fy = a22 * gyp + a21 * gyl + b2 * (half * (sp + _ghost(sp, 1)))
+    fy[-1] = 0                                       # no flux through the pole faces
+    fys = np.zeros_like(fy)
+    fys[1:] = fy[:-1]
+    return (fx - np.roll(fx, 1, axis=1)) / dlam + (fy - fys) / dphi - C * sp
+
+
+def split_phi(phi):
+    """(Phi_hat, Phi_tilde) of a refresh: Phi_hat = fp32(Phi), Phi_tilde =
+    fp32(Phi - Phi_hat) with the difference taken in double precision."""
+    phi = np.asarray(phi, dtype=np.float64)
+    hat = phi.astype(np.float32)
+    return hat, (phi - hat.astype(np.float64)).astype(np.float32)
