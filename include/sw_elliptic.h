@@ -187,11 +187,14 @@ sw_status sw_ensemble_solve(int n, const sw_grid *grids, const sw_solve_opts *o,
  * `stream` and the call returns at once.  stats_dev (device, n entries, may
  * be NULL) receives the members' sw_solve_stats when the solve completes on
  * the stream; the return value reports only argument and enqueue errors.
- * Nothing is allocated once each grid's workspace exists, i.e. after one
- * solve with the same precision and k (or an attached workspace), so the
- * call can then be recorded in a CUDA graph and replayed.  A replay uses the
- * member descriptors of the recorded call, which each grid keeps in pinned
- * host memory until its next sw_ensemble_solve_async.  Not for
+ * Calls may follow one another without synchronisation, on the same grids
+ * too: each grid stages the descriptors of a call in one of four pinned host
+ * slots, and a call waits on the host only while the stream is four calls
+ * behind.  Nothing is allocated once each grid's workspace exists, i.e.
+ * after one solve with the same precision and k (or an attached workspace),
+ * so the call can then be recorded in a CUDA graph and replayed.  A recorded
+ * call stages into a slot of its own, which replays read; it stays valid
+ * until the grid's next recorded sw_ensemble_solve_async.  Not for
  * SW_PC_LEARNED. */
 sw_status sw_ensemble_solve_async(int n, const sw_grid *grids, const sw_solve_opts *o,
                                   const double *const *R, double *const *phi,

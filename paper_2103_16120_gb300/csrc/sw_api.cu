@@ -53,10 +53,20 @@ struct sw_grid_s {
     EnsDesc *desc;                 // device: launch descriptor when this grid leads a launch
     EnsDesc *h_desc;               // pinned host staging of desc
     MemberCtl *h_ctl;              // pinned host copies read after a solve
-    void *h_mdev;                  // pinned staging of the member descriptor (async solves)
+    void *h_mdev;                  // pinned staging of the member descriptor (recorded async solves)
     GlobalCtl *h_g;
     double *h_eta;
+    // async solves outside a graph capture: a ring of pinned staging slots
+    // (member descriptor + launch descriptor), each reused only after the
+    // copies that read it have run (its event)
+    unsigned char *h_ring;
+    cudaEvent_t ring_ev[4];
+    int ring_next;
 };
+
+constexpr int RING = 4;
+
+static size_t ring_slot_bytes() { return ((sizeof(SolverBlock::dev) + 255) & ~(size_t)255) + sizeof(EnsDesc); }
 
 GridView sw::grid_view(const sw_grid_s *g)
 {
@@ -119,12 +129,18 @@ extern "C" sw_status sw_grid_create(int nx, int ny, double radius, sw_grid *out)
     if (e == cudaSuccess) e = cudaMallocHost((void **)&g->h_desc, sizeof(EnsDesc));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&g->h_ctl, sizeof(MemberCtl) + sizeof(GlobalCtl) + 64);
     if (e == cudaSuccess) e = cudaMallocHost(&g->h_mdev, sizeof(SolverBlock::dev));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&g->h_ring, RING * ring_slot_bytes());
+    int nev = 0;
+    for (; e == cudaSuccess && nev < RING; ++nev) e = cudaEventCreateWithFlags(&g->ring_ev[nev], cudaEventDisableTiming);
     if (e != cudaSuccess) {
         if (g->cmem) cudaFree(g->cmem);
         if (g->blk) cudaFree(g->blk);
         if (g->desc) cudaFree(g->desc);
         if (g->h_desc) cudaFreeHost(g->h_desc);
         if (g->h_ctl) cudaFreeHost(g->h_ctl);
+        if (g->h_mdev) cudaFreeHost(g->h_mdev);
+        if (g->h_ring) cudaFreeHost(g->h_ring);
+        for (int q = 0; q + 1 < nev; ++q) cudaEventDestroy(g->ring_ev[q]);
         delete g;
         return cuda_fail(e, "sw_grid_create");
     }
@@ -153,6 +169,8 @@ extern "C" sw_status sw_grid_destroy(sw_grid g)
     if (g->ws_owned && g->ws) cudaFree(g->ws);
     cudaFreeHost(g->h_ctl);
     cudaFreeHost(g->h_mdev);
+    cudaFreeHost(g->h_ring);
+    for (int q = 0; q < RING; ++q) cudaEventDestroy(g->ring_ev[q]);
     delete g;
     return SW_OK;
 }
@@ -799,6 +817,15 @@ extern "C" sw_status sw_ensemble_solve_async(int n, const sw_grid *grids, const 
     int max_nx = 0;
     if ((st = check_members(n, grids, o, R, phi, max_nx))) return st;
     cudaStream_t s = (cudaStream_t)stream;
+    // host staging: a recorded call uses each grid's dedicated slot, which a
+    // graph replay reads; otherwise the next ring slot, once the copies of
+    // its previous use have run
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(s, &cap));
+    const bool recorded = (cap != cudaStreamCaptureStatusNone);
+    auto mdev_slot = [&](sw_grid g) -> void * {
+        return recorded ? g->h_mdev : (void *)(g->h_ring + (size_t)g->ring_next * ring_slot_bytes());
+    };
     for (int m = 0; m < n; ++m) {
         sw_grid g = grids[m];
         if (o->eta > 0.0 && o->eta != g->eta_explicit) {
@@ -806,27 +833,39 @@ extern "C" sw_status sw_ensemble_solve_async(int n, const sw_grid *grids, const 
             if ((st = refactor(g, s))) return st;
         }
         if ((st = ensure_ws(g, o->prec, o->k))) return st;
+        if (!recorded) CK(cudaEventSynchronize(g->ring_ev[g->ring_next]));
+        void *hm = mdev_slot(g);
         if (o->prec == SW_PREC_FP64) {
             MemberDev<PolFP64> M;
             fill_member<PolFP64>(g, o, R[m], phi[m], M);
-            std::memcpy(g->h_mdev, &M, sizeof(M));
+            std::memcpy(hm, &M, sizeof(M));
         } else if (o->prec == SW_PREC_MIXED_FP16) {
             MemberDev<PolF16> M;
             fill_member<PolF16>(g, o, R[m], phi[m], M);
-            std::memcpy(g->h_mdev, &M, sizeof(M));
+            std::memcpy(hm, &M, sizeof(M));
         } else {
             MemberDev<PolBF16> M;
             fill_member<PolBF16>(g, o, R[m], phi[m], M);
-            std::memcpy(g->h_mdev, &M, sizeof(M));
+            std::memcpy(hm, &M, sizeof(M));
         }
-        CK(cudaMemcpyAsync(g->blk->dev, g->h_mdev, member_dev_bytes(o->prec), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(g->blk->dev, hm, member_dev_bytes(o->prec), cudaMemcpyHostToDevice, s));
     }
     if (o->res_history) CK(launch_fill(o->res_history, (size_t)o->max_iters + 1, NAN, s));
     Plan P;
     if ((st = plan_launch(n, grids, o, max_nx, P))) return st;
     sw_grid lead = grids[0];
-    fill_desc(*lead->h_desc, n, grids, P);
-    CK(cudaMemcpyAsync(lead->desc, lead->h_desc, sizeof(EnsDesc), cudaMemcpyHostToDevice, s));
+    EnsDesc *hd = recorded ? lead->h_desc
+                           : (EnsDesc *)((unsigned char *)mdev_slot(lead) +
+                                         ((sizeof(SolverBlock::dev) + 255) & ~(size_t)255));
+    fill_desc(*hd, n, grids, P);
+    CK(cudaMemcpyAsync(lead->desc, hd, sizeof(EnsDesc), cudaMemcpyHostToDevice, s));
+    if (!recorded) {
+        for (int m = 0; m < n; ++m) {
+            sw_grid g = grids[m];
+            CK(cudaEventRecord(g->ring_ev[g->ring_next], s));
+            g->ring_next = (g->ring_next + 1) % RING;
+        }
+    }
     CK(launch_init_members(lead->desc, n, s));
     CK(launch_gcr(o->prec, o->k, P.minb, lead->desc, P.grid, max_nx, P.threads, P.smem, s));
     if (stats_dev) CK(launch_member_stats(lead->desc, n, stats_dev, s));

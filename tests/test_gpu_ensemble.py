@@ -52,6 +52,38 @@ def test_async_equals_sync(prec):
         assert torch.equal(p, q)
 
 
+def test_back_to_back_async_solves_of_one_grid():
+    """A warm-started sequence enqueued without synchronisation: each call
+    stages its descriptors in the grid's ring of pinned slots, so later calls
+    (more of them than the ring holds) cannot overwrite what an earlier,
+    not yet executed, copy reads.  Each step between the solves changes the
+    coefficients too."""
+    nx, ny, n = 256, 128, 7
+    Ps = [synth.sequence_problem(nx, ny, 9100, t) for t in range(n)]
+    cos = [[torch.as_tensor(P[k], device="cuda") for k in sw.COEFF_KEYS] for P in Ps]
+    Rs = [torch.as_tensor(P["R"], device="cuda") for P in Ps]
+    o = sw.sw_solve_opts_default(prec=sw.SW_PREC_MIXED_FP16, tol=1e-8)
+    g = sw.sw_grid_create(nx, ny)
+    ref, phi = [], torch.zeros_like(Rs[0])
+    for t in range(n):
+        sw.sw_elliptic_set_coeffs(g, *cos[t])
+        st = sw.sw_gcr_solve(g, o, Rs[t], phi)
+        assert st.status == sw.SW_OK
+        ref.append((phi.clone(), st.iterations))
+    bufs = [sw.stats_buffer(1) for _ in range(n)]
+    outs, phi = [], torch.zeros_like(Rs[0])
+    torch.cuda.synchronize()
+    for t in range(n):
+        sw.sw_elliptic_set_coeffs(g, *cos[t])
+        sw.sw_ensemble_solve_async([g], o, [Rs[t]], [phi], bufs[t])
+        outs.append(phi.clone())                          # stream-ordered copy
+    torch.cuda.synchronize()
+    for t in range(n):
+        got = sw.stats_from_device(bufs[t], 1)[0]
+        assert got.status == sw.SW_OK and got.iterations == ref[t][1]
+        assert torch.equal(outs[t], ref[t][0])
+
+
 def test_graph_capture_and_replay():
     grids, Rs = members()
     o = sw.sw_solve_opts_default(prec=sw.SW_PREC_MIXED_FP16, tol=1e-8)
