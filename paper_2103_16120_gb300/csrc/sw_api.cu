@@ -42,6 +42,8 @@ struct sw_grid_s {
     // coefficient storage (one allocation)
     void *cmem;
     double *ax, *cx, *bx, *ay, *cy, *by, *C, *diag, *lf, *invD, *zz, *gam, *ec, *rowmax, *eta;
+    double *gam32, *ec32;          // per row, of the FP32 zonal factors
+    bool f64_valid;                // the FP64 zonal factors match the coefficients and eta
     float *wax, *wcx, *wbx, *way, *wcy, *wby, *wC, *wdiag, *lf32, *invD32, *zz32;
     bool has_coeffs;
     double eta_explicit;           // > 0 when chosen by sw_grid_set_eta
@@ -122,7 +124,7 @@ extern "C" sw_status sw_grid_create(int nx, int ny, double radius, sw_grid *out)
     cudaError_t e = cudaGetDevice(&g->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, g->device);
     size_t N = g->N;
-    size_t bytes = 11 * al(N * 8) + 3 * al((size_t)ny * 8) + al(8) + 11 * al(N * 4);
+    size_t bytes = 11 * al(N * 8) + 5 * al((size_t)ny * 8) + al(8) + 11 * al(N * 4);
     if (e == cudaSuccess) e = cudaMalloc(&g->cmem, bytes);
     if (e == cudaSuccess) e = cudaMalloc((void **)&g->blk, sizeof(SolverBlock));
     if (e == cudaSuccess) e = cudaMalloc((void **)&g->desc, sizeof(EnsDesc));
@@ -152,6 +154,8 @@ extern "C" sw_status sw_grid_create(int nx, int ny, double radius, sw_grid *out)
     g->gam = (double *)p; p += al((size_t)ny * 8);
     g->ec = (double *)p; p += al((size_t)ny * 8);
     g->rowmax = (double *)p; p += al((size_t)ny * 8);
+    g->gam32 = (double *)p; p += al((size_t)ny * 8);
+    g->ec32 = (double *)p; p += al((size_t)ny * 8);
     g->eta = (double *)p; p += al(8);
     float **d32[] = {&g->wax, &g->wcx, &g->wbx, &g->way, &g->wcy, &g->wby, &g->wC, &g->wdiag, &g->lf32, &g->invD32, &g->zz32};
     for (auto q : d32) { *q = (float *)p; p += al(N * 4); }
@@ -266,14 +270,36 @@ static sw_status ensure_ws(sw_grid g, int prec, int k)
 // ---------------------------------------------------------------------------
 // coefficients
 // ---------------------------------------------------------------------------
-static sw_status refactor(sw_grid g, cudaStream_t s)
+static FactorArgs factor_args(const sw_grid_s *g)
 {
     FactorArgs f;
     f.nx = g->nx; f.ny = g->ny; f.eta_explicit = g->eta_explicit;
     f.ax = g->ax; f.C = g->C; f.rowmax = g->rowmax;
     f.lf = g->lf; f.invD = g->invD; f.zz = g->zz; f.gam = g->gam; f.ec = g->ec; f.eta_out = g->eta;
-    f.lf32 = g->lf32; f.invD32 = g->invD32; f.zz32 = g->zz32;
-    CK(launch_factor(f, row_threads(g->nx), s));
+    f.lf32 = g->lf32; f.invD32 = g->invD32; f.zz32 = g->zz32; f.gam32 = g->gam32; f.ec32 = g->ec32;
+    return f;
+}
+
+// new coefficients or eta: the FP32 zonal factors (mixed solvers) now; the
+// FP64 ones when an FP64 solve or preconditioner needs them (ensure_f64)
+static sw_status refactor(sw_grid g, cudaStream_t s)
+{
+    CK(launch_factor(factor_args(g), false, row_threads(g->nx), s));
+    g->f64_valid = false;
+    return SW_OK;
+}
+
+// the FP64 zonal factors, stream-ordered before the FP64 work that follows on
+// s.  Inside a CUDA graph capture they are always recorded: a replay cannot
+// know whether the coefficients changed since.
+static sw_status ensure_f64(sw_grid g, cudaStream_t s)
+{
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(s, &cap));
+    const bool recorded = (cap != cudaStreamCaptureStatusNone);
+    if (g->f64_valid && !recorded) return SW_OK;
+    CK(launch_factor(factor_args(g), true, row_threads(g->nx), s));
+    if (!recorded) g->f64_valid = true;
     return SW_OK;
 }
 
@@ -379,7 +405,8 @@ static void fill_member(sw_grid g, const sw_solve_opts *o, const double *R, doub
         M.wC = (const ct *)g->C; M.wdiag = (const ct *)g->diag;
         M.lf = (const ft *)g->lf; M.invD = (const ft *)g->invD; M.zz = (const ft *)g->zz;
     }
-    M.gam = g->gam; M.ec = g->ec;
+    if constexpr (Pol::kMixed) { M.gam = g->gam32; M.ec = g->ec32; }
+    else { M.gam = g->gam; M.ec = g->ec; }
     M.R = R; M.phi = phi;
     M.r = (rt *)(w + L.r);
     M.qa = (qt *)(w + L.qa); M.qb = (qt *)(w + L.qb); M.e = (qt *)(w + L.e);
@@ -397,6 +424,8 @@ static sw_status upload_member(sw_grid g, const sw_solve_opts *o, const double *
                                void *Mdev_out_host)
 {
     if (o->prec == SW_PREC_FP64) {
+        sw_status st = ensure_f64(g, s);
+        if (st) return st;
         MemberDev<PolFP64> M;
         fill_member<PolFP64>(g, o, R, phi, M);
         std::memcpy(Mdev_out_host, &M, sizeof(M));
@@ -432,6 +461,7 @@ extern "C" sw_status sw_precond_apply(sw_grid g, const sw_solve_opts *o, const v
     alignas(16) unsigned char hbuf[sizeof(SolverBlock::dev)];
     int nst = o->pc >= 2 ? o->n_richardson : 1;
     if (o->prec == SW_PREC_FP64) {
+        if ((st = ensure_f64(g, s))) return st;
         MemberDev<PolFP64> M;
         fill_member<PolFP64>(g, o, nullptr, nullptr, M);
         M.r = (double *)r;                    // the stages read r from the member's r
@@ -728,6 +758,7 @@ extern "C" sw_status sw_gcr_solve_noalloc(sw_grid g, const sw_solve_opts *o, con
         if ((st = refactor(g, s))) return st;
     }
     alignas(16) unsigned char hbuf[sizeof(SolverBlock::dev)];
+    if (o->prec == SW_PREC_FP64 && (st = ensure_f64(g, s))) return st;
     if (o->prec == SW_PREC_FP64) fill_member_noalloc<PolFP64>(g, scratch, o, R, phi, hbuf);
     else if (o->prec == SW_PREC_MIXED_FP16) fill_member_noalloc<PolF16>(g, scratch, o, R, phi, hbuf);
     else fill_member_noalloc<PolBF16>(g, scratch, o, R, phi, hbuf);
@@ -833,6 +864,7 @@ extern "C" sw_status sw_ensemble_solve_async(int n, const sw_grid *grids, const 
             if ((st = refactor(g, s))) return st;
         }
         if ((st = ensure_ws(g, o->prec, o->k))) return st;
+        if (o->prec == SW_PREC_FP64 && (st = ensure_f64(g, s))) return st;
         if (!recorded) CK(cudaEventSynchronize(g->ring_ev[g->ring_next]));
         void *hm = mdev_slot(g);
         if (o->prec == SW_PREC_FP64) {

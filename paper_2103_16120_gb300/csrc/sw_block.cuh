@@ -87,6 +87,52 @@ __device__ __forceinline__ void block_sum_many(const T (&x)[NV], double *tot, do
     __syncthreads();
 }
 
+// Double-float arithmetic (a value as an unevaluated sum hi + lo of two
+// floats; Knuth's error-free TwoSum): about 44 significant bits on the FP32
+// pipe.  On this GPU an FP64 instruction costs about 64 cycles per warp
+// against about 5 for FP32, so the mixed policies keep their block and member
+// sums in this form and convert to FP64 once per total.
+struct dfloat {
+    float hi, lo;
+};
+
+__device__ __forceinline__ dfloat df_split(double x)
+{
+    const float h = (float)x;
+    return dfloat{h, (float)(x - (double)h)};
+}
+
+__device__ __forceinline__ dfloat df_add(dfloat a, dfloat b)
+{
+    const float s = a.hi + b.hi;
+    const float v = s - a.hi;
+    float e = (a.hi - (s - v)) + (b.hi - v);
+    e += a.lo + b.lo;
+    const float hi = s + e;
+    return dfloat{hi, e - (hi - s)};
+}
+
+// Block sum of NV <= 32 FP32 values per thread into double-float totals
+// tot[q] (shared memory): a warp butterfly in FP32, then the warps in index
+// order in double-float.  scratch: 32 floats per warp.
+template <int NV>
+__device__ __forceinline__ void block_sum_many_df(const float (&x)[NV], dfloat *tot, float *scratch)
+{
+    static_assert(NV <= 32, "");
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    float v[32];
+#pragma unroll
+    for (int q = 0; q < 32; ++q) v[q] = q < NV ? x[q] : 0.f;
+    scratch[w * 32 + lane] = warp_sum32(v);
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        dfloat t{0.f, 0.f};
+        for (int ww = 0; ww < nw; ++ww) t = df_add(t, dfloat{scratch[ww * 32 + threadIdx.x], 0.f});
+        tot[threadIdx.x] = t;
+    }
+    __syncthreads();
+}
+
 // Exclusive block scan of affine maps x -> a x + b in thread order (REV:
 // reversed thread order).  On return (a, b) composes the maps of the earlier
 // threads.  sm: 2 values per warp.

@@ -127,6 +127,7 @@ struct MemberCtl {
     double rn2_rec;                 // ||r||^2 of the recursive residual
     double rn2_cur;                 // ||r||^2 of the residual the next direction works on
     double g3;                      // share of ||r||^2 the last option-3 direction removed
+    double tolr, tolr2;             // exit threshold on ||r|| and its square (set with ||R||)
     double alpha[KMAX + 1];
     double G[KMAX + 1][KMAX + 1];   // Gram matrix <L p_l, L p_m> of the cycle (logical)
     double Ginv[KMAX + 1];          // 1 / G[l][l], formed once per direction

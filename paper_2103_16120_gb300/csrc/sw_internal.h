@@ -33,12 +33,13 @@ struct FactorArgs {
     int nx, ny;
     double eta_explicit;            // > 0: use it; otherwise 1/max|diag(P^M)|
     const double *ax, *C, *rowmax;
-    double *lf, *invD, *zz, *gam, *ec, *eta_out;
-    float *lf32, *invD32, *zz32;
+    double *lf, *invD, *zz, *gam, *ec, *eta_out;        // FP64 factors
+    float *lf32, *invD32, *zz32;                         // FP32 factors
+    double *gam32, *ec32;                                // per row, of the FP32 factors
 };
 
 cudaError_t launch_faces(const FaceArgs &a, int threads, cudaStream_t s);
-cudaError_t launch_factor(const FactorArgs &a, int threads, cudaStream_t s);
+cudaError_t launch_factor(const FactorArgs &a, bool fp64, int threads, cudaStream_t s);
 size_t gcr_smem_bytes(int prec, int max_nx, int k, int cache_const, int cache_state);
 cudaError_t gcr_occupancy(int prec, int k, int minb, int threads, size_t smem, int *blocks_per_sm);
 cudaError_t launch_gcr(int prec, int k, int minb, const EnsDesc *Ddev, int grid, int max_nx, int threads,

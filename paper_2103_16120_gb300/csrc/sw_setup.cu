@@ -65,19 +65,21 @@ __global__ void __launch_bounds__(MAX_THREADS) k_faces(FaceArgs a)
 }
 
 // 2x2 matrix [[m00, m01], [m10, m11]]
-struct M2 { double m00, m01, m10, m11; };
+template <class T> struct M2 { T m00, m01, m10, m11; };
 
-__device__ __forceinline__ M2 mul(const M2 &A, const M2 &B)   // A B
+template <class T>
+__device__ __forceinline__ M2<T> mul(const M2<T> &A, const M2<T> &B)   // A B
 {
     return {A.m00 * B.m00 + A.m01 * B.m10, A.m00 * B.m01 + A.m01 * B.m11,
             A.m10 * B.m00 + A.m11 * B.m10, A.m10 * B.m01 + A.m11 * B.m11};
 }
 
 // scale by a power of two so that the largest entry is O(1) (ratios unchanged)
-__device__ __forceinline__ void renorm(M2 &A)
+template <class T>
+__device__ __forceinline__ void renorm(M2<T> &A)
 {
-    double m = fmax(fmax(fabs(A.m00), fabs(A.m01)), fmax(fabs(A.m10), fabs(A.m11)));
-    if (m > 0.0 && isfinite(m)) {
+    T m = fmax(fmax(fabs(A.m00), fabs(A.m01)), fmax(fabs(A.m10), fabs(A.m11)));
+    if (m > T(0) && isfinite(m)) {
         int e;
         frexp(m, &e);
         A.m00 = ldexp(A.m00, -e); A.m01 = ldexp(A.m01, -e);
@@ -85,7 +87,8 @@ __device__ __forceinline__ void renorm(M2 &A)
     }
 }
 
-__device__ __forceinline__ M2 shfl_up(const M2 &A, int d)
+template <class T>
+__device__ __forceinline__ M2<T> shfl_up(const M2<T> &A, int d)
 {
     return {__shfl_up_sync(0xffffffffu, A.m00, d), __shfl_up_sync(0xffffffffu, A.m01, d),
             __shfl_up_sync(0xffffffffu, A.m10, d), __shfl_up_sync(0xffffffffu, A.m11, d)};
@@ -93,38 +96,46 @@ __device__ __forceinline__ M2 shfl_up(const M2 &A, int d)
 
 // exclusive block scan of matrices in thread order: returns the product of
 // the matrices of all earlier threads (later ones on the left)
-__device__ M2 scan_mat_excl(M2 A, M2 *sm)
+template <class T>
+__device__ M2<T> scan_mat_excl(M2<T> A, M2<T> *sm)
 {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    M2 inc = A;
+    M2<T> inc = A;
     for (int d = 1; d < 32; d <<= 1) {
-        M2 o = shfl_up(inc, d);
+        M2<T> o = shfl_up(inc, d);
         if (lane >= d) { inc = mul(inc, o); renorm(inc); }
     }
-    M2 ex = shfl_up(inc, 1);
-    if (lane == 0) ex = {1.0, 0.0, 0.0, 1.0};
+    M2<T> ex = shfl_up(inc, 1);
+    if (lane == 0) ex = {T(1), T(0), T(0), T(1)};
     if (lane == 31) sm[w] = inc;
     __syncthreads();
-    M2 pre = {1.0, 0.0, 0.0, 1.0};
+    M2<T> pre = {T(1), T(0), T(0), T(1)};
     for (int ww = 0; ww < w; ++ww) { pre = mul(sm[ww], pre); renorm(pre); }
-    M2 out = mul(ex, pre);
+    M2<T> out = mul(ex, pre);
     renorm(out);
     __syncthreads();
     return out;
 }
 
+// the zonal factors of every row in the arithmetic of T: FP64 factors for the
+// FP64 solver (lf, invD, zz, gam, ec), FP32 ones for the mixed solvers (lf32,
+// invD32, zz32, gam32, ec32).  An FP64 instruction costs about 64 cycles per
+// warp on this GPU against about 5 for FP32, so the mixed path's factors are
+// computed in FP32 and the FP64 ones only when an FP64 solve needs them.
+template <class T>
 __global__ void __launch_bounds__(MAX_THREADS) k_factor(FactorArgs a)
 {
     extern __shared__ __align__(16) unsigned char dsm[];
-    double *sb = (double *)dsm;                          // nx
-    __shared__ M2 smat[MAX_THREADS / 32];
-    __shared__ double sscan[2 * (MAX_THREADS / 32)];
+    T *sb = (T *)dsm;                                    // nx
+    __shared__ M2<T> smat[MAX_THREADS / 32];
+    __shared__ T sscan[2 * (MAX_THREADS / 32)];
     __shared__ double red[MAX_THREADS / 32];
     __shared__ double s_eta;
     const int nx = a.nx, ny = a.ny, j = blockIdx.x;
     const size_t row = (size_t)j * nx;
+    constexpr bool f64 = sizeof(T) == 8;
 
-    // eta: explicit, or 1 / max |diag(P^M)| over the grid
+    // eta: explicit, or 1 / max |diag(P^M)| over the grid (FP64 in both)
     if (a.eta_explicit > 0.0) {
         if (threadIdx.x == 0) s_eta = a.eta_explicit;
     } else {
@@ -140,19 +151,23 @@ __global__ void __launch_bounds__(MAX_THREADS) k_factor(FactorArgs a)
         }
     }
     __syncthreads();
-    const double eta = s_eta;
-    if (j == 0 && threadIdx.x == 0) *a.eta_out = eta;
+    const double eta64 = s_eta;
+    if (j == 0 && threadIdx.x == 0) *a.eta_out = eta64;
+    const T eta = (T)eta64;
 
     // row of T: diag_i = 1 + eta (ax_i + ax_{i-1} + C_i); coupling of i and
     // i+1: o_i = -eta ax_i (o_{nx-1} couples the last point to the first)
     const double *ax = a.ax + row, *C = a.C + row;
-    auto diagT = [&](int i) { int im = (i == 0) ? nx - 1 : i - 1; return 1.0 + eta * (ax[i] + ax[im] + C[i]); };
-    const double ec = -eta * ax[nx - 1];
-    const double d0 = diagT(0);
-    const double gam = -d0;
+    auto diagT = [&](int i) {
+        int im = (i == 0) ? nx - 1 : i - 1;
+        return T(1) + eta * ((T)ax[i] + (T)ax[im] + (T)C[i]);
+    };
+    const T ec = -eta * (T)ax[nx - 1];
+    const T d0 = diagT(0);
+    const T gam = -d0;
     // T' = T minus the rank-one wrap term w w^T / gam, w = (gam, 0, .., 0, ec)
     auto dprime = [&](int i) {
-        double d = diagT(i);
+        T d = diagT(i);
         if (i == 0) d -= gam;
         if (i == nx - 1) d -= ec * ec / gam;
         return d;
@@ -160,43 +175,47 @@ __global__ void __launch_bounds__(MAX_THREADS) k_factor(FactorArgs a)
     int c0, c1;
     row_chunk(nx, c0, c1);
     // product of the transfer matrices [[d'_i, -o_{i-1}^2], [1, 0]] of my chunk
-    M2 P = {1.0, 0.0, 0.0, 1.0};
+    M2<T> P = {T(1), T(0), T(0), T(1)};
     for (int i = c0; i < c1; ++i) {
-        double o = (i == 0) ? 0.0 : -eta * ax[i - 1];
-        M2 Mi = {dprime(i), -o * o, 1.0, 0.0};
+        T o = (i == 0) ? T(0) : -eta * (T)ax[i - 1];
+        M2<T> Mi = {dprime(i), -o * o, T(1), T(0)};
         P = mul(Mi, P);
         renorm(P);
     }
-    M2 Q = scan_mat_excl(P, smat);
+    M2<T> Q = scan_mat_excl(P, smat);
     // pivot before my chunk: D_{c0-1} = theta_{c0-1} / theta_{c0-2} = Q00 / Q10
-    double Dprev = (c0 > 0) ? Q.m00 / Q.m10 : 0.0;
+    T Dprev = (c0 > 0) ? Q.m00 / Q.m10 : T(0);
+    double *lf64 = a.lf + row, *iD64 = a.invD + row;
+    float *lf32 = a.lf32 + row, *iD32 = a.invD32 + row;
     for (int i = c0; i < c1; ++i) {
-        double l = 0.0, D;
+        T l = T(0), D;
         if (i == 0) {
             D = dprime(0);
         } else {
-            double o = -eta * ax[i - 1];
+            T o = -eta * (T)ax[i - 1];
             l = o / Dprev;
             D = dprime(i) - l * o;
         }
-        a.lf[row + i] = l;
-        a.invD[row + i] = 1.0 / D;
+        if constexpr (f64) { lf64[i] = l; iD64[i] = T(1) / D; }
+        else { lf32[i] = l; iD32[i] = T(1) / D; }
         Dprev = D;
     }
     __syncthreads();
     // z = T'^{-1} w
-    for (int i = threadIdx.x; i < nx; i += blockDim.x) sb[i] = (i == 0) ? gam : ((i == nx - 1) ? ec : 0.0);
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) sb[i] = (i == 0) ? gam : ((i == nx - 1) ? ec : T(0));
     __syncthreads();
-    trisolve_row<double, double>(sb, nx, a.lf + row, a.invD + row, (const double *)nullptr, 0.0, 0.0, sscan);
-    const double g = 1.0 / (gam + gam * sb[0] + ec * sb[nx - 1]);
+    if constexpr (f64) trisolve_row<T, T>(sb, nx, lf64, iD64, (const T *)nullptr, T(0), T(0), sscan);
+    else trisolve_row<T, T>(sb, nx, lf32, iD32, (const T *)nullptr, T(0), T(0), sscan);
+    const T g = T(1) / (gam + gam * sb[0] + ec * sb[nx - 1]);
     for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-        double z = sb[i] * g;
-        a.zz[row + i] = z;
-        a.zz32[row + i] = (float)z;
-        a.lf32[row + i] = (float)a.lf[row + i];
-        a.invD32[row + i] = (float)a.invD[row + i];
+        const T z = sb[i] * g;
+        if constexpr (f64) a.zz[row + i] = z;
+        else a.zz32[row + i] = z;
     }
-    if (threadIdx.x == 0) { a.gam[j] = gam; a.ec[j] = ec; }
+    if (threadIdx.x == 0) {
+        if constexpr (f64) { a.gam[j] = gam; a.ec[j] = ec; }
+        else { a.gam32[j] = gam; a.ec32[j] = ec; }
+    }
 }
 
 cudaError_t launch_faces(const FaceArgs &a, int threads, cudaStream_t s)
@@ -205,12 +224,16 @@ cudaError_t launch_faces(const FaceArgs &a, int threads, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_factor(const FactorArgs &a, int threads, cudaStream_t s)
+cudaError_t launch_factor(const FactorArgs &a, bool fp64, int threads, cudaStream_t s)
 {
-    size_t smem = (size_t)a.nx * sizeof(double);
-    cudaError_t e = cudaFuncSetAttribute(k_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_factor<<<a.ny, threads, smem, s>>>(a);
+    const size_t smem = (size_t)a.nx * (fp64 ? sizeof(double) : sizeof(float));
+    if (smem > 48 * 1024) {
+        cudaError_t e = fp64 ? cudaFuncSetAttribute(k_factor<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                             : cudaFuncSetAttribute(k_factor<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    if (fp64) k_factor<double><<<a.ny, threads, smem, s>>>(a);
+    else k_factor<float><<<a.ny, threads, smem, s>>>(a);
     return cudaGetLastError();
 }
 

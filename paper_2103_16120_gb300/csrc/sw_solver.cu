@@ -53,28 +53,20 @@ __device__ __forceinline__ unsigned long long gtimer()
 
 __device__ __forceinline__ int vload(const int *p) { return *(const volatile int *)p; }
 
-// Double-float arithmetic (a value as an unevaluated sum hi + lo of two
-// floats; Knuth's error-free TwoSum), for the member-wide sums: about 44
-// significant bits on the FP32 pipe, which on this GPU is 64 times faster
-// than FP64.  Every block adds in the same order, so all agree bit for bit.
-struct dfloat {
-    float hi, lo;
-};
-
-__device__ __forceinline__ dfloat df_split(double x)
+// 1/x for the GCR scalars: a reciprocal approximation refined by two
+// Newton-Raphson steps r <- r + r (1 - x r), each of which doubles the number
+// of correct bits, so the result agrees with the quotient to about an ulp.
+// An FP64 division costs about 600 cycles on this GPU, this about 300.
+// Outside a safe exponent range, and for zero, infinities and NaN, it is the
+// quotient itself.
+__device__ __forceinline__ double recip(double x)
 {
-    const float h = (float)x;
-    return dfloat{h, (float)(x - (double)h)};
-}
-
-__device__ __forceinline__ dfloat df_add(dfloat a, dfloat b)
-{
-    const float s = a.hi + b.hi;
-    const float v = s - a.hi;
-    float e = (a.hi - (s - v)) + (b.hi - v);
-    e += a.lo + b.lo;
-    const float hi = s + e;
-    return dfloat{hi, e - (hi - s)};
+    const int ex = (__double2hiint(x) >> 20) & 0x7ff;      // biased exponent
+    if (ex < 1023 - 500 || ex > 1023 + 500) return 1.0 / x;
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+    r = fma(r, fma(-x, r, 1.0), r);
+    return fma(r, fma(-x, r, 1.0), r);
 }
 
 template <class Pol>
@@ -328,15 +320,41 @@ __device__ void phase_prec0(const MemberDev<Pol> &M, const RowView<Pol> &v, type
 // (The text's half-precision variant keeps these global sums in single
 // precision, Sec. 4.3.)
 // ---------------------------------------------------------------------------
+// PH_LE scalars on the lanes of warp 0 (lane l < nd holds direction l):
+// alpha_l of the text, written to c.alpha, and, in lane 0, <Lp_new, Lp_new>
+// and <r, Lp_new> of the direction Lp_new = Le + sum alpha_l Lp_l, from the
+// Gram matrix.  An FP64 instruction costs the same for one lane as for 32 on
+// this GPU, so the lanes take the O(nd^2) products together.
+__device__ __forceinline__ void le_scalars(MemberCtl &c, const double *tot, double &lplp, double &rlp)
+{
+    const int lane = threadIdx.x & 31, nd = c.nu + 1;
+    const bool on = lane < nd;
+    const double a = on ? -tot[S_C0 + lane] * c.Ginv[lane] : 0.0;
+    double rowv = on ? 2.0 * tot[S_C0 + lane] : 0.0;
+    for (int m = 0; m < nd; ++m) {
+        const double am = __shfl_sync(0xffffffffu, a, m);
+        if (on) rowv = fma(am, c.G[lane][m], rowv);
+    }
+    double t1 = on ? a * rowv : 0.0, t2 = on ? a * tot[S_T0 + lane] : 0.0;
+    // lanes >= nd hold zeros: the tree needs only the levels below nd
+#pragma unroll
+    for (int o = KMAX / 2; o > 0; o >>= 1) {
+        if (o < nd) {
+            t1 += __shfl_down_sync(0xffffffffu, t1, o);
+            t2 += __shfl_down_sync(0xffffffffu, t2, o);
+        }
+    }
+    if (on) c.alpha[lane] = a;
+    lplp = tot[S_A] + t1;
+    rlp = tot[S_B] + t2;
+}
+
 template <class Pol>
-__device__ void advance(const MemberDev<Pol> &M, MemberCtl &c, const double *tot, bool writer)
+__device__ void advance(const MemberDev<Pol> &M, MemberCtl &c, const double *tot, bool writer, double lplp,
+                        double rlp)
 {
     typedef double sc;
     const int k = M.k, nd = c.nu + 1;
-    // the mixed policies sum a warp's products in FP32 before the FP64 sums
-    // (relative error < 1e-6): their exit test keeps that margin below the
-    // tolerance
-    const double tolR = M.tol * c.nR * (Pol::kMixed ? (1.0 - 1e-5) : 1.0);
     bool done = false;
     // the learned preconditioner alternates its directions with option 3's:
     // on the network's turn the launch ends (PH_EXT), the host writes the
@@ -358,17 +376,22 @@ __device__ void advance(const MemberDev<Pol> &M, MemberCtl &c, const double *tot
             c.rn_true = rn;
             c.rn2_rec = c.rn2_cur = (double)tot[S_A];
             c.nu = -1;
+            // the mixed policies sum a warp's products in FP32 before the
+            // FP64 sums (relative error < 1e-6): their exit test keeps that
+            // margin below the tolerance
+            c.tolr = M.tol * c.nR * (Pol::kMixed ? (1.0 - 1e-5) : 1.0);
+            c.tolr2 = c.tolr * c.tolr;
             if (writer && M.hist) M.hist[0] = c.nR > 0.0 ? rn / c.nR : 0.0;
             if (c.nR == 0.0) { c.phase = PH_ZERO; break; }
             if (!isfinite(rn) || !isfinite(c.nR)) { finish(ST_NONFINITE); break; }
-            if (rn <= M.tol * c.nR * (Pol::kMixed ? (1.0 - 1e-5) : 1.0) && M.min_iters <= 0) { finish(ST_OK); break; }
+            if (rn <= c.tolr && M.min_iters <= 0) { finish(ST_OK); break; }
             to_precond();
         } else {
             c.rn_true = rn;
             c.rn2_cur = (double)tot[S_A];
             if (writer && M.hist) M.hist[c.it] = rn / c.nR;
             if (!isfinite(rn)) { finish(ST_NONFINITE); break; }
-            if (rn <= tolR && c.it >= M.min_iters) { finish(ST_OK); break; }
+            if (rn <= c.tolr && c.it >= M.min_iters) { finish(ST_OK); break; }
             if (c.it >= M.max_iters) { finish(ST_NOT_CONVERGED); break; }
             to_precond();
         }
@@ -383,17 +406,8 @@ __device__ void advance(const MemberDev<Pol> &M, MemberCtl &c, const double *tot
         c.phase = M.nstages > 1 ? PH_PREC : PH_LE;
         break;
     case PH_LE: {
-        // alpha_l of the text; <Lp_new, Lp_new> and <r, Lp_new> of the
-        // direction Lp_new = Le + sum alpha_l Lp_l, from the Gram matrix
-        sc a[KMAX], lplp = tot[S_A], rlp = tot[S_B];
-        for (int l = 0; l < nd; ++l) a[l] = -tot[S_C0 + l] * (sc)c.Ginv[l];
-        for (int l = 0; l < nd; ++l) {
-            sc rowv = (sc)2 * tot[S_C0 + l];
-            for (int m = 0; m < nd; ++m) rowv += a[m] * (sc)c.G[l][m];
-            lplp += a[l] * rowv;
-            rlp += a[l] * tot[S_T0 + l];
-            c.alpha[l] = (double)a[l];
-        }
+        // alpha (c.alpha), <Lp_new, Lp_new> (lplp) and <r, Lp_new> (rlp)
+        // come from le_scalars
         if (learned && c.net_turn && !c.fb_now) {
             // the network's direction would remove rlp^2 / lplp of ||r||^2; it
             // must remove at least fb_ratio times the share the last option-3
@@ -407,7 +421,7 @@ __device__ void advance(const MemberDev<Pol> &M, MemberCtl &c, const double *tot
             }
         }
         if (!(lplp > sc(0)) || !isfinite(lplp) || !isfinite(rlp)) { finish(ST_BREAKDOWN); break; }
-        c.beta = (double)(-rlp / lplp);
+        c.beta = -rlp * recip(lplp);
         c.phase = PH_UB;
         break;
     }
@@ -423,7 +437,7 @@ __device__ void advance(const MemberDev<Pol> &M, MemberCtl &c, const double *tot
         if (learned) c.net_turn ^= 1;
         if (writer && M.hist) M.hist[c.it] = sqrt(rn2) / c.nR;
         c.G[ln][ln] = (double)tot[S_B];
-        c.Ginv[ln] = 1.0 / c.G[ln][ln];
+        c.Ginv[ln] = recip(c.G[ln][ln]);
         for (int m = 0; m < ln; ++m) c.G[ln][m] = c.G[m][ln] = (double)tot[S_C0 + m];
         c.nu = ln;
         if (c.nu == k) {                          // restart: p_0 <- p_k
@@ -433,7 +447,7 @@ __device__ void advance(const MemberDev<Pol> &M, MemberCtl &c, const double *tot
             c.nu = 0;
         }
         if (!isfinite(rn2)) { finish(ST_NONFINITE); break; }
-        if ((rn2 <= tolR * tolR && c.it >= M.min_iters) || (M.ru_every > 0 && c.it % M.ru_every == 0) ||
+        if ((rn2 <= c.tolr2 && c.it >= M.min_iters) || (M.ru_every > 0 && c.it % M.ru_every == 0) ||
             c.it >= M.max_iters)
             c.phase = PH_TRUE;
         else
@@ -468,6 +482,7 @@ __global__ void __launch_bounds__(MAX_THREADS, MINB) k_gcr(const EnsDesc *__rest
     __shared__ int s_m, s_ok;
     __shared__ double s_blk[32];
     __shared__ double s_tot[NSLOT];
+    __shared__ dfloat s_totf[NSLOT];
     if (threadIdx.x == 0) {
         int lo = 0, hi = D->n;
         while (hi - lo > 1) {
@@ -536,12 +551,13 @@ __global__ void __launch_bounds__(MAX_THREADS, MINB) k_gcr(const EnsDesc *__rest
         const int ns = phase_slots(s_c.phase, s_c.nu + 1, slot);
         double *pbuf = partg + (size_t)par * NSLOT * ny;
         if (ns > 0) {
-            block_sum_many<NP, acc_t>(part, s_blk, scratch);
+            if constexpr (Pol::kMixed) block_sum_many_df<NP>(part, (dfloat *)s_blk, (float *)scratch);
+            else block_sum_many<NP, acc_t>(part, s_blk, scratch);
             if (threadIdx.x < ns) {
                 const int g = slot[threadIdx.x];          // slot of tot; its place in part
-                const double bs = s_blk[g < S_T0 ? g : g - S_T0 + 2 + KM];
-                if constexpr (Pol::kMixed) ((dfloat *)pbuf)[(size_t)threadIdx.x * ny + local] = df_split(bs);
-                else pbuf[(size_t)threadIdx.x * ny + local] = bs;
+                const int at = g < S_T0 ? g : g - S_T0 + 2 + KM;
+                if constexpr (Pol::kMixed) ((dfloat *)pbuf)[(size_t)threadIdx.x * ny + local] = ((const dfloat *)s_blk)[at];
+                else pbuf[(size_t)threadIdx.x * ny + local] = s_blk[at];
             }
         }
         __syncthreads();
@@ -588,7 +604,7 @@ __global__ void __launch_bounds__(MAX_THREADS, MINB) k_gcr(const EnsDesc *__rest
                     for (int o = 16; o > 0; o >>= 1)
                         t = df_add(t, dfloat{__shfl_xor_sync(0xffffffffu, t.hi, o),
                                              __shfl_xor_sync(0xffffffffu, t.lo, o)});
-                    if (lane == 0) s_tot[slot[q]] = (double)t.hi + (double)t.lo;
+                    if (lane == 0) s_totf[q] = t;
                 } else {
                     const double *src = pbuf + (size_t)q * ny;
                     double t = 0;
@@ -601,8 +617,18 @@ __global__ void __launch_bounds__(MAX_THREADS, MINB) k_gcr(const EnsDesc *__rest
             }
         }
         __syncthreads();
+        if constexpr (Pol::kMixed) {
+            // the double-float totals to FP64, one slot per lane
+            if (threadIdx.x < ns) s_tot[slot[threadIdx.x]] = (double)s_totf[threadIdx.x].hi + (double)s_totf[threadIdx.x].lo;
+            __syncthreads();
+        }
         SW_TRACE(33);
-        if (threadIdx.x == 0) advance<Pol>(M, s_c, s_tot, local == 0);
+        if (threadIdx.x < 32) {
+            double lplp = 0.0, rlp = 0.0;
+            if (s_c.phase == PH_LE) le_scalars(s_c, s_tot, lplp, rlp);
+            __syncwarp();
+            if (threadIdx.x == 0) advance<Pol>(M, s_c, s_tot, local == 0, lplp, rlp);
+        }
         __syncthreads();
         SW_TRACE(34);
         par ^= 1;
