@@ -627,7 +627,9 @@ __global__ void __launch_bounds__(MAX_THREADS, MINB) k_gcr(const EnsDesc *__rest
             double lplp = 0.0, rlp = 0.0;
             if (s_c.phase == PH_LE) le_scalars(s_c, s_tot, lplp, rlp);
             __syncwarp();
+            SW_TRACE(35);
             if (threadIdx.x == 0) advance<Pol>(M, s_c, s_tot, local == 0, lplp, rlp);
+            SW_TRACE(36);
         }
         __syncthreads();
         SW_TRACE(34);

@@ -8,8 +8,9 @@ between consecutive tags, per tag pair.
 
 Tags: 10 + phase at the start of a phase (phases: 0 true residual, 1 update,
 2 Richardson stage, 3 L(e)), 30 after the row work, 31 after the block sums,
-32 after the member barrier, 33 after the member sums, 34 after the state
-transition; inside the rows 101/102 (L(e): staging, stencil), 201 (update
+32 after the member barrier, 33 after the member sums, 35 after the L(e)
+scalars, 36 after the state transition, 34 after the block has synchronised;
+inside the rows 101/102 (L(e): staging, stencil), 201 (update
 loop), 301/302/303 (stage: staging, stencil, zonal solve), 401/402 (first
 stage: zonal solve, store).
 
