@@ -348,7 +348,7 @@ def run_gpu(args):
     except Exception:
         pass
     peak = peaks.get("hbm_gbs", 6800.0)
-    launches_per_step = 5   # k_faces, k_factor, k_init_members, k_gcr, k_member_stats
+    launches_per_step = 4   # k_faces, k_factor<float>, k_init_members, k_gcr
     if rank == 0:
         print(json.dumps({
             "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,

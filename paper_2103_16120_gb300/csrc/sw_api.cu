@@ -551,9 +551,10 @@ static sw_status plan_launch(int n, const sw_grid *grids, const sw_solve_opts *o
     return SW_OK;
 }
 
-static void fill_desc(EnsDesc &D, int n, const sw_grid *grids, const Plan &P)
+static void fill_desc(EnsDesc &D, int n, const sw_grid *grids, const Plan &P, sw_solve_stats *stats = nullptr)
 {
     D.n = n;
+    D.stats = stats;
     D.grid = P.grid;
     D.cache_const = P.cc;
     D.cache_state = P.cs;
@@ -800,6 +801,7 @@ extern "C" sw_status sw_gcr_solve_noalloc(sw_grid g, const sw_solve_opts *o, con
     D.grid = grid;
     D.cache_const = cc;
     D.cache_state = cs;
+    D.stats = nullptr;
     D.cta_begin[0] = 0;
     D.cta_begin[1] = grid;
     D.blk[0] = g->blk;
@@ -889,7 +891,7 @@ extern "C" sw_status sw_ensemble_solve_async(int n, const sw_grid *grids, const 
     EnsDesc *hd = recorded ? lead->h_desc
                            : (EnsDesc *)((unsigned char *)mdev_slot(lead) +
                                          ((sizeof(SolverBlock::dev) + 255) & ~(size_t)255));
-    fill_desc(*hd, n, grids, P);
+    fill_desc(*hd, n, grids, P, stats_dev);
     CK(cudaMemcpyAsync(lead->desc, hd, sizeof(EnsDesc), cudaMemcpyHostToDevice, s));
     if (!recorded) {
         for (int m = 0; m < n; ++m) {
@@ -900,7 +902,6 @@ extern "C" sw_status sw_ensemble_solve_async(int n, const sw_grid *grids, const 
     }
     CK(launch_init_members(lead->desc, n, s));
     CK(launch_gcr(o->prec, o->k, P.minb, lead->desc, P.grid, max_nx, P.threads, P.smem, s));
-    if (stats_dev) CK(launch_member_stats(lead->desc, n, stats_dev, s));
     return SW_OK;
 }
 

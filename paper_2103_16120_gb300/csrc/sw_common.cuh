@@ -8,6 +8,8 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include "../../include/sw_elliptic.h"
+
 namespace sw {
 
 constexpr int KMAX = 8;             // largest GCR k
@@ -151,6 +153,7 @@ struct alignas(256) SolverBlock {
 struct EnsDesc {
     int n, grid;
     int cache_const, cache_state;   // row constants / owner-only vectors in shared memory
+    sw_solve_stats *stats;          // device, n entries, or null: each member's stats at the end
     int cta_begin[MAX_MEMBERS + 1];
     SolverBlock *blk[MAX_MEMBERS];
 };

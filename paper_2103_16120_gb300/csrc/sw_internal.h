@@ -52,8 +52,6 @@ cudaError_t launch_fill(double *p, size_t n, double v, cudaStream_t s);
 cudaError_t set_barrier_debug(unsigned long long extra, unsigned long long limit_ns);
 // every member of a launch descriptor: initial GCR state, cleared barrier
 cudaError_t launch_init_members(const EnsDesc *Ddev, int n, cudaStream_t s);
-// every member's sw_solve_stats, written to device memory
-cudaError_t launch_member_stats(const EnsDesc *Ddev, int n, sw_solve_stats *out, cudaStream_t s);
 // the member's e from an FP32 field (the network's direction)
 cudaError_t launch_store_e(int prec, const void *Mdev, const float *ef, int nx, int ny, int threads, cudaStream_t s);
 // the learned preconditioner applied to the residual r (FP64 or FP32) of

@@ -17,29 +17,31 @@ __global__ void __launch_bounds__(MAX_THREADS) k_faces(FaceArgs a)
 {
     __shared__ double red[MAX_THREADS / 32];
     const int nx = a.nx, ny = a.ny, j = blockIdx.x;
-    const double idl2 = 1.0 / (a.dlam * a.dlam), idp2 = 1.0 / (a.dphi * a.dphi);
-    const double i4 = 1.0 / (4.0 * a.dlam * a.dphi), i2l = 1.0 / (2.0 * a.dlam), i2p = 1.0 / (2.0 * a.dphi);
+    // the face scales, each with the 1/2 of the face mean folded in (a power
+    // of two: the products round exactly as (a + b)/2 times the scale)
+    const double idl2 = 0.5 / (a.dlam * a.dlam), idp2 = 0.5 / (a.dphi * a.dphi);
+    const double i4 = 0.5 / (4.0 * a.dlam * a.dphi), i2l = 0.5 / (2.0 * a.dlam), i2p = 0.5 / (2.0 * a.dphi);
     const size_t row = (size_t)j * nx;
     double m = 0.0;
     for (int i = threadIdx.x; i < nx; i += blockDim.x) {
         const int ip = (i + 1 == nx) ? 0 : i + 1, im = (i == 0) ? nx - 1 : i - 1;
         const size_t id = row + i;
         // x faces i+1/2 and i-1/2 of row j
-        double ax = 0.5 * (a.A11[id] + a.A11[row + ip]) * idl2;
-        double cx = 0.5 * (a.A12[id] + a.A12[row + ip]) * i4;
-        double bx = 0.5 * (a.B1[id] + a.B1[row + ip]) * i2l;
-        double axm = 0.5 * (a.A11[row + im] + a.A11[id]) * idl2;
-        double bxm = 0.5 * (a.B1[row + im] + a.B1[id]) * i2l;
+        double ax = (a.A11[id] + a.A11[row + ip]) * idl2;
+        double cx = (a.A12[id] + a.A12[row + ip]) * i4;
+        double bx = (a.B1[id] + a.B1[row + ip]) * i2l;
+        double axm = (a.A11[row + im] + a.A11[id]) * idl2;
+        double bxm = (a.B1[row + im] + a.B1[id]) * i2l;
         // y faces j+1/2 and j-1/2 (zero through the pole faces)
         double ay = 0.0, cy = 0.0, by = 0.0, ays = 0.0, bys = 0.0;
         if (j < ny - 1) {
-            ay = 0.5 * (a.A22[id] + a.A22[id + nx]) * idp2;
-            cy = 0.5 * (a.A21[id] + a.A21[id + nx]) * i4;
-            by = 0.5 * (a.B2[id] + a.B2[id + nx]) * i2p;
+            ay = (a.A22[id] + a.A22[id + nx]) * idp2;
+            cy = (a.A21[id] + a.A21[id + nx]) * i4;
+            by = (a.B2[id] + a.B2[id + nx]) * i2p;
         }
         if (j > 0) {
-            ays = 0.5 * (a.A22[id - nx] + a.A22[id]) * idp2;
-            bys = 0.5 * (a.B2[id - nx] + a.B2[id]) * i2p;
+            ays = (a.A22[id - nx] + a.A22[id]) * idp2;
+            bys = (a.B2[id - nx] + a.B2[id]) * i2p;
         }
         const double c = a.C[id];
         // diagonal of P^M = L - P^Z + P^H, and of L

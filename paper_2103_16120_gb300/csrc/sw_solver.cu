@@ -639,6 +639,22 @@ __global__ void __launch_bounds__(MAX_THREADS, MINB) k_gcr(const EnsDesc *__rest
         const int *src = (const int *)&s_c;
         int *dst = (int *)&B->ctl;
         for (int q = 0; q < (int)(sizeof(MemberCtl) / 4); ++q) dst[q] = src[q];
+        if (D->stats) {
+            // the member's sw_solve_stats (a block that passed every member
+            // barrier has seen any abort)
+            const int st = vload(&G->abort) ? ST_TIMEOUT : (s_c.phase == PH_DONE ? s_c.status : ST_INTERNAL);
+            sw_solve_stats S = {};
+            S.iterations = s_c.it;
+            S.converged = (st == ST_OK);
+            S.status = st;
+            S.fallbacks = s_c.fallbacks;
+            S.r0_norm = s_c.r0;
+            S.R_norm = s_c.nR;
+            S.true_rel_residual = s_c.nR > 0 ? s_c.rn_true / s_c.nR : 0.0;
+            S.recursive_rel_residual = s_c.nR > 0 ? sqrt(s_c.rn2_rec) / s_c.nR : 0.0;
+            S.eta = *M.etap;
+            D->stats[m] = S;
+        }
     }
     // per-row norms of the final true residual
     if (ok && s_c.phase == PH_DONE && M.rowres && (s_c.status == ST_OK || s_c.status == ST_NOT_CONVERGED)) {
@@ -873,40 +889,12 @@ __global__ void k_init_members(const EnsDesc *D)
     B->g.where = 0;
 }
 
-__global__ void k_member_stats(const EnsDesc *D, sw_solve_stats *out)
-{
-    const int m = blockIdx.x * blockDim.x + threadIdx.x;
-    if (m >= D->n) return;
-    const SolverBlock *B = D->blk[m];
-    const MemberCtl &c = B->ctl;
-    // the members' descriptors share their leading fields whatever the policy
-    const MemberDev<PolFP64> *M = (const MemberDev<PolFP64> *)B->dev;
-    const bool timeout = B->g.abort != 0;
-    const int st = timeout ? ST_TIMEOUT : (c.phase == PH_DONE ? c.status : ST_INTERNAL);
-    sw_solve_stats S = {};
-    S.iterations = c.it;
-    S.converged = (st == ST_OK);
-    S.status = st;
-    S.fallbacks = c.fallbacks;
-    S.r0_norm = c.r0;
-    S.R_norm = c.nR;
-    S.true_rel_residual = c.nR > 0 ? c.rn_true / c.nR : 0.0;
-    S.recursive_rel_residual = c.nR > 0 ? sqrt(c.rn2_rec) / c.nR : 0.0;
-    S.eta = *M->etap;
-    out[m] = S;
-}
-
 cudaError_t launch_init_members(const EnsDesc *Ddev, int n, cudaStream_t s)
 {
     k_init_members<<<(n + 127) / 128, 128, 0, s>>>(Ddev);
     return cudaGetLastError();
 }
 
-cudaError_t launch_member_stats(const EnsDesc *Ddev, int n, sw_solve_stats *out, cudaStream_t s)
-{
-    k_member_stats<<<(n + 127) / 128, 128, 0, s>>>(Ddev, out);
-    return cudaGetLastError();
-}
 
 #ifdef SW_PHASE_TRACE
 // configure the device timeline (traced builds only): buffer of 2*cap words
