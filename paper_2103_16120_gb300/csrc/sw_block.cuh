@@ -96,12 +96,6 @@ struct dfloat {
     float hi, lo;
 };
 
-__device__ __forceinline__ dfloat df_split(double x)
-{
-    const float h = (float)x;
-    return dfloat{h, (float)(x - (double)h)};
-}
-
 __device__ __forceinline__ dfloat df_add(dfloat a, dfloat b)
 {
     const float s = a.hi + b.hi;

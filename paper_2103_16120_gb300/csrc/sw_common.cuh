@@ -63,8 +63,10 @@ struct PolBF16 {
 
 // accumulation type of each thread's inner-product partials and of the warp
 // sums: FP64 for the FP64 policy, FP32 for the mixed policies (at most 32
-// threads' partials of a few products each).  The block sums over warps, the
-// member sums over blocks and the GCR scalars are FP64 for every policy.
+// threads' partials of a few products each).  The mixed policies add the
+// warps and the blocks in double-float (sw_block.cuh) and convert each total
+// to FP64 once; the FP64 policy adds in FP64.  The GCR scalars are FP64 for
+// every policy.
 template <class Pol> struct Acc { typedef double type; };
 template <> struct Acc<PolF16> { typedef float type; };
 template <> struct Acc<PolBF16> { typedef float type; };

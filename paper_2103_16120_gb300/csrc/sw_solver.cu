@@ -315,7 +315,7 @@ __device__ void phase_prec0(const MemberDev<Pol> &M, const RowView<Pol> &v, type
 }
 
 // ---------------------------------------------------------------------------
-// state transition after a phase, from the member-wide FP64 sums tot[slot].
+// state transition after a phase, from the member-wide sums tot[slot] (FP64).
 // The scalars (alpha, beta, the Gram update, norms) are FP64 for every policy.
 // (The text's half-precision variant keeps these global sums in single
 // precision, Sec. 4.3.)
