@@ -5,7 +5,9 @@ The oracle recomputes, in FP64 and with its own operator, the residual
 * the 2048 x 1024 problem (config 4), mixed FP16;
 * all 64 members of the ensemble (config 2), solved in one launch;
 * the first steps of the 512 x 256 warm-started sequence (config 1), whose
-  solution is also compared with the oracle's own GCR solution.
+  solution is also compared with the oracle's own GCR solution;
+* FP64 iterates on 1024 x 512 and 2048 x 1024, where every block owns several
+  rows, against the oracle's iterates (1e-12).
 
 The GPU's exit test uses its FP64 true residual at tol = 1e-8.  The oracle
 recomputes the same quantity in another summation order, so the bar is
@@ -82,3 +84,34 @@ def test_sequence_512x256_warm_start():
         assert oracle_rel_residual(P, x) <= 1.001 * TOL
     ref, _ = O.Problem(P).gcr(P["R"], O.Opts(k=4, tol=1e-13, max_iters=5000))
     assert np.linalg.norm(x - ref) <= 1e-6 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("nx,ny,iters", [(1024, 512, 6), (2048, 1024, 5)])
+def test_multirow_blocks_fp64_fixed_iterations(nx, ny, iters):
+    """Grids whose rows outnumber the resident blocks: every block owns several
+    rows, reads them through global memory and runs the instantiation built for
+    two resident blocks per SM.  FP64 iterates after a fixed number of
+    iterations against the oracle's.
+
+    The bar comes from the conditioning.  One rounding of R (relative 1e-16)
+    moves the oracle's own iterates by s: 6e-16 at 512 x 256, 4e-14 at
+    1024 x 512, 1e-11 at 2048 x 1024, where the zonal coefficients near the
+    poles reach 1e15.  The GPU rounds differently in every operation, so it
+    may differ by a hundred such roundings: max(1e-12, 100 s)."""
+    P = synth.problem(nx, ny, 5100 + nx)
+    g = grid_for(P)
+    R = torch.as_tensor(P["R"], device="cuda")
+    phi = torch.zeros_like(R)
+    o = sw.sw_solve_opts_default(k=4, tol=0.0, max_iters=iters)
+    st = sw.sw_gcr_solve(g, o, R, phi)
+    assert st.iterations == iters and st.status == sw.SW_ERR_NOT_CONVERGED
+    prob = O.Problem(P)
+    oo = O.Opts(k=4, tol=0.0, max_iters=iters, eta=st.eta)
+    ref, _ = prob.gcr(P["R"], oo)
+    R1 = P["R"] * (1.0 + 1e-16 * np.random.default_rng(1).standard_normal(P["R"].shape))
+    ref1, _ = prob.gcr(R1, oo)
+    nref = np.linalg.norm(ref)
+    s = np.linalg.norm(ref1 - ref) / nref
+    err = np.linalg.norm(phi.cpu().numpy() - ref) / nref
+    print(f"{nx}x{ny}: GPU vs oracle {err:.2e}, oracle under one rounding of R {s:.2e}")
+    assert err <= max(1e-12, 100.0 * s)
