@@ -7,7 +7,8 @@ The oracle recomputes, in FP64 and with its own operator, the residual
 * the first steps of the 512 x 256 warm-started sequence (config 1), whose
   solution is also compared with the oracle's own GCR solution;
 * FP64 iterates on 1024 x 512 and 2048 x 1024, where every block owns several
-  rows, against the oracle's iterates (1e-12).
+  rows, against the oracle's iterates (1e-12);
+* the largest row the library takes, 4096 x 2048, mixed FP16.
 
 The GPU's exit test uses its FP64 true residual at tol = 1e-8.  The oracle
 recomputes the same quantity in another summation order, so the bar is
@@ -115,3 +116,17 @@ def test_multirow_blocks_fp64_fixed_iterations(nx, ny, iters):
     err = np.linalg.norm(phi.cpu().numpy() - ref) / nref
     print(f"{nx}x{ny}: GPU vs oracle {err:.2e}, oracle under one rounding of R {s:.2e}")
     assert err <= max(1e-12, 100.0 * s)
+
+
+def test_largest_grid_4096x2048_mixed():
+    """The largest row the library takes (nx = 4096: 256 threads with 16 points
+    each in the zonal scans), every block owning many rows.  The oracle
+    recomputes the true residual of the GPU's solution."""
+    P = synth.problem(4096, 2048, 5300)
+    g = grid_for(P)
+    R = torch.as_tensor(P["R"], device="cuda")
+    phi = torch.zeros_like(R)
+    st = sw.sw_gcr_solve(g, sw.sw_solve_opts_default(prec=sw.SW_PREC_MIXED_FP16, tol=TOL, max_iters=6000), R, phi)
+    print(f"4096x2048 mixed: {st.iterations} iterations, true residual {st.true_rel_residual:.2e}")
+    assert st.status == sw.SW_OK and st.true_rel_residual <= TOL
+    assert oracle_rel_residual(P, phi.cpu().numpy()) <= 1.001 * TOL
