@@ -696,6 +696,96 @@ __global__ void __launch_bounds__(MAX_THREADS) k_operator(OpArgs<CT> a, const T 
     stencil_row<T, CT>(s3, s3 + nx, s3 + 2 * nx, nx, j, ny, c, true, y + row, false);
 }
 
+// Standalone operator for rows of a multiple of 8 points: a thread computes 4
+// consecutive points from vector loads, all issued before the arithmetic (one
+// round trip): the three rows of x with a point of halo on each side (the
+// rows beyond a pole are the pole row shifted by half a circle, which keeps
+// 4-point alignment when nx/2 is a multiple of 4) and the face coefficients.
+// Each zonal face flux is formed once and used by both of its points (the
+// same expression as in stencil_row, so the result is the same).
+template <class T>
+__device__ __forceinline__ void ld4(const T *p, T (&v)[4])
+{
+    if constexpr (sizeof(T) == 4) {
+        const float4 q = __ldg((const float4 *)p);
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    } else {
+        const double2 q0 = __ldg((const double2 *)p), q1 = __ldg((const double2 *)p + 1);
+        v[0] = q0.x; v[1] = q0.y; v[2] = q1.x; v[3] = q1.y;
+    }
+}
+
+template <class T>
+__device__ __forceinline__ void st4(T *p, const T (&v)[4])
+{
+    if constexpr (sizeof(T) == 4) {
+        *(float4 *)p = make_float4(v[0], v[1], v[2], v[3]);
+    } else {
+        ((double2 *)p)[0] = make_double2(v[0], v[1]);
+        ((double2 *)p)[1] = make_double2(v[2], v[3]);
+    }
+}
+
+// values k = 0..5 at longitudes i0 - 1 + k of a row shifted by sh (periodic)
+template <class T>
+__device__ __forceinline__ void ld6(const T *rowp, int i0, int sh, int nx, T (&v)[6])
+{
+    int a = i0 + sh;
+    if (a >= nx) a -= nx;
+    T m[4];
+    ld4(rowp + a, m);
+    v[1] = m[0]; v[2] = m[1]; v[3] = m[2]; v[4] = m[3];
+    v[0] = __ldg(rowp + (a == 0 ? nx - 1 : a - 1));
+    v[5] = __ldg(rowp + (a + 4 == nx ? 0 : a + 4));
+}
+
+template <class T, class CT>
+__global__ void __launch_bounds__(128) k_operator4(OpArgs<CT> a, const T *__restrict__ x, T *__restrict__ y)
+{
+    const int nx = a.nx, ny = a.ny, j = blockIdx.y;
+    const int i0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (i0 >= nx) return;
+    const size_t row = (size_t)j * nx, rs = j > 0 ? row - nx : row;
+    const bool has_n = j < ny - 1, has_s = j > 0;
+    int srcS, shS, srcN, shN;
+    ghost_row(j - 1, nx, ny, srcS, shS);
+    ghost_row(j + 1, nx, ny, srcN, shN);
+    T xc[6], xn[6], xs[6];
+    ld6(x + row, i0, 0, nx, xc);
+    ld6(x + (size_t)srcN * nx, i0, shN, nx, xn);
+    ld6(x + (size_t)srcS * nx, i0, shS, nx, xs);
+    // zonal faces i0 - 1 .. i0 + 3 (index 0 = face i0 - 1/2)
+    const int iw = i0 == 0 ? nx - 1 : i0 - 1;
+    CT ax[5], cx[5], bx[5], q[4];
+    ax[0] = __ldg(a.ax + row + iw); cx[0] = __ldg(a.cx + row + iw); bx[0] = __ldg(a.bx + row + iw);
+    ld4(a.ax + row + i0, q); for (int k = 0; k < 4; ++k) ax[k + 1] = q[k];
+    ld4(a.cx + row + i0, q); for (int k = 0; k < 4; ++k) cx[k + 1] = q[k];
+    ld4(a.bx + row + i0, q); for (int k = 0; k < 4; ++k) bx[k + 1] = q[k];
+    CT ay[4] = {}, cy[4] = {}, by[4] = {}, ays[4] = {}, cys[4] = {}, bys[4] = {}, cc[4];
+    if (has_n) { ld4(a.ay + row + i0, ay); ld4(a.cy + row + i0, cy); ld4(a.by + row + i0, by); }
+    if (has_s) { ld4(a.ay + rs + i0, ays); ld4(a.cy + rs + i0, cys); ld4(a.by + rs + i0, bys); }
+    ld4(a.C + row + i0, cc);
+    // zonal fluxes: face m (m = 0..4) lies between points m - 1 and m of the
+    // 6-point windows (window index k = longitude i0 - 1 + k)
+    T F[5];
+#pragma unroll
+    for (int m = 0; m < 5; ++m)
+        F[m] = (T)cx[m] * (xn[m] + xn[m + 1] - xs[m] - xs[m + 1]) + (T)bx[m] * (xc[m] + xc[m + 1]) +
+               (T)ax[m] * (xc[m + 1] - xc[m]);
+    T out[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int k = u + 1;                      // window index of the point
+        T v = F[u + 1] - F[u];
+        if (has_n) v += (T)ay[u] * (xn[k] - xc[k]) + (T)cy[u] * (xc[k + 1] + xn[k + 1] - xc[k - 1] - xn[k - 1]) +
+                        (T)by[u] * (xc[k] + xn[k]);
+        if (has_s) v -= (T)ays[u] * (xc[k] - xs[k]) + (T)cys[u] * (xs[k + 1] + xc[k + 1] - xs[k - 1] - xc[k - 1]) +
+                        (T)bys[u] * (xs[k] + xc[k]);
+        out[u] = v - (T)cc[u] * xc[k];
+    }
+    st4(y + row + i0, out);
+}
+
 // one preconditioner stage of every row (stage 0 from the residual r)
 template <class Pol>
 __global__ void __launch_bounds__(MAX_THREADS) k_precond(const MemberDev<Pol> *Mp, int mu)
@@ -812,8 +902,20 @@ cudaError_t launch_gcr(int prec, int k, int minb, const EnsDesc *Ddev, int grid,
     return cudaLaunchCooperativeKernel(f, dim3(grid), dim3(threads), args, smem, s);
 }
 
+template <class T>
+static bool op4_ok(const OpArgs<T> &a, const T *x, const T *y)
+{
+    auto al = [](const void *p) { return ((uintptr_t)p & 15) == 0; };
+    return a.nx % 8 == 0 && a.ny <= 65535 && al(x) && al(y) && al(a.ax) && al(a.cx) && al(a.bx) && al(a.ay) &&
+           al(a.cy) && al(a.by) && al(a.C);
+}
+
 cudaError_t launch_operator_f64(const OpArgs<double> &a, const double *x, double *y, int threads, cudaStream_t s)
 {
+    if (op4_ok(a, x, y)) {
+        k_operator4<double, double><<<dim3((a.nx / 4 + 127) / 128, a.ny), 128, 0, s>>>(a, x, y);
+        return cudaGetLastError();
+    }
     size_t smem = 3 * (size_t)a.nx * sizeof(double);
     cudaError_t e = cudaFuncSetAttribute(k_operator<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -823,6 +925,10 @@ cudaError_t launch_operator_f64(const OpArgs<double> &a, const double *x, double
 
 cudaError_t launch_operator_f32(const OpArgs<float> &a, const float *x, float *y, int threads, cudaStream_t s)
 {
+    if (op4_ok(a, x, y)) {
+        k_operator4<float, float><<<dim3((a.nx / 4 + 127) / 128, a.ny), 128, 0, s>>>(a, x, y);
+        return cudaGetLastError();
+    }
     size_t smem = 3 * (size_t)a.nx * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(k_operator<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
