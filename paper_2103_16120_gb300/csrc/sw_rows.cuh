@@ -220,6 +220,87 @@ __device__ __noinline__ void stencil_row(const T *S, const T *X, const T *N, int
     __syncthreads();
 }
 
+// stencil_row for rows of a multiple of 4 points (16-byte aligned rows and
+// coefficients): a thread takes 4 consecutive points per pass, reads them
+// with vector loads, and forms each zonal face flux once for its two points.
+// The expressions are those of stencil_row, so the results are the same.
+template <class T>
+__device__ __forceinline__ void ldv4(const T *p, T (&v)[4])
+{
+    if constexpr (sizeof(T) == 4) {
+        const float4 q = *(const float4 *)p;
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    } else {
+        const double2 q0 = ((const double2 *)p)[0], q1 = ((const double2 *)p)[1];
+        v[0] = q0.x; v[1] = q0.y; v[2] = q1.x; v[3] = q1.y;
+    }
+}
+
+template <class T>
+__device__ __forceinline__ void ldw6(const T *rowp, int i0, int nx, T (&v)[6])
+{
+    T m[4];
+    ldv4(rowp + i0, m);
+    v[1] = m[0]; v[2] = m[1]; v[3] = m[2]; v[4] = m[3];
+    v[0] = rowp[i0 == 0 ? nx - 1 : i0 - 1];
+    v[5] = rowp[i0 + 4 == nx ? 0 : i0 + 4];
+}
+
+template <class T, class CT>
+__device__ __noinline__ void stencil_row4(const T *S, const T *X, const T *N, int nx, int j, int ny,
+                                          const RowCoef<CT> c, bool full, T *y, bool ypad)
+{
+    const bool has_n = j < ny - 1, has_s = j > 0;
+    for (int i0 = 4 * threadIdx.x; i0 < nx; i0 += 4 * blockDim.x) {
+        T xc[6], xn[6], xs[6];
+        ldw6(X, i0, nx, xc);
+        ldw6(N, i0, nx, xn);
+        ldw6(S, i0, nx, xs);
+        const int iw = i0 == 0 ? nx - 1 : i0 - 1;
+        CT ax[5] = {}, cx[5], bx[5], q[4];
+        cx[0] = c.cx[iw]; bx[0] = c.bx[iw];
+        ldv4(c.cx + i0, q); for (int k = 0; k < 4; ++k) cx[k + 1] = q[k];
+        ldv4(c.bx + i0, q); for (int k = 0; k < 4; ++k) bx[k + 1] = q[k];
+        CT cc[4] = {};
+        if (full) {
+            ax[0] = c.ax[iw];
+            ldv4(c.ax + i0, q); for (int k = 0; k < 4; ++k) ax[k + 1] = q[k];
+            ldv4(c.C + i0, cc);
+        }
+        CT ay[4] = {}, cy[4] = {}, by[4] = {}, ays[4] = {}, cys[4] = {}, bys[4] = {};
+        if (has_n) { ldv4(c.ay + i0, ay); ldv4(c.cy + i0, cy); ldv4(c.by + i0, by); }
+        if (has_s) { ldv4(c.ays + i0, ays); ldv4(c.cys + i0, cys); ldv4(c.bys + i0, bys); }
+        // face m (m = 0..4) between window points m - 1 and m (window k = longitude i0 - 1 + k)
+        T F[5];
+#pragma unroll
+        for (int m = 0; m < 5; ++m)
+            F[m] = (T)cx[m] * (xn[m] + xn[m + 1] - xs[m] - xs[m + 1]) + (T)bx[m] * (xc[m] + xc[m + 1]) +
+                   (T)ax[m] * (xc[m + 1] - xc[m]);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int k = u + 1;
+            T v = F[u + 1] - F[u];
+            if (has_n) v += (T)ay[u] * (xn[k] - xc[k]) + (T)cy[u] * (xc[k + 1] + xn[k + 1] - xc[k - 1] - xn[k - 1]) +
+                            (T)by[u] * (xc[k] + xn[k]);
+            if (has_s) v -= (T)ays[u] * (xc[k] - xs[k]) + (T)cys[u] * (xs[k + 1] + xc[k + 1] - xs[k - 1] - xc[k - 1]) +
+                            (T)bys[u] * (xs[k] + xc[k]);
+            const int i = i0 + u;
+            y[ypad ? pidx(i) : i] = v - (T)cc[u] * xc[k];
+        }
+    }
+    __syncthreads();
+}
+
+// the vector stencil needs rows of a multiple of 4 points and 16-byte aligned
+// coefficient rows
+template <class CT>
+__device__ __forceinline__ bool stencil4_ok(const RowCoef<CT> &c, int nx)
+{
+    auto al = [](const void *p) { return ((uintptr_t)p & 15) == 0; };
+    return (nx & 3) == 0 && al(c.cx) && al(c.bx) && al(c.ax) && al(c.C) && al(c.ay) && al(c.cy) && al(c.by) &&
+           al(c.ays) && al(c.cys) && al(c.bys);
+}
+
 template <class Pol>
 __device__ __forceinline__ bool in_band(const MemberDev<Pol> &M, int j)
 {
@@ -412,7 +493,10 @@ __device__ void precond_stage(const MemberDev<Pol> &M, const RowView<Pol> &v, ty
     SW_TRACE(301);
     const comp *S = stg, *X = stg + nx, *N = stg + 2 * nx;
     const bool opt3 = (M.pc >= 3);
-    stencil_row<comp, typename Pol::coef>(S, X, N, nx, j, ny, coef_of(v), !opt3, sb, true);
+    if (stencil4_ok(coef_of(v), nx))
+        stencil_row4<comp, typename Pol::coef>(S, X, N, nx, j, ny, coef_of(v), !opt3, sb, true);
+    else
+        stencil_row<comp, typename Pol::coef>(S, X, N, nx, j, ny, coef_of(v), !opt3, sb, true);
     constexpr int U = batch_of<comp>();
     for (int i0 = threadIdx.x; i0 < nx; i0 += U * blockDim.x) {
         comp rv[U], dg[U];

@@ -190,8 +190,12 @@ __device__ void phase_le(const MemberDev<Pol> &M, const MemberCtl &c, const RowV
     SW_TRACE(101);
     const comp *stg = (const comp *)ws;
     // L e of the row, straight into the row's L e storage
-    stencil_row<comp, typename Pol::coef>(stg, stg + nx, stg + 2 * nx, nx, j, ny, coef_of(v), true, (comp *)v.Le,
-                                          false);
+    if (stencil4_ok(coef_of(v), nx) && ((uintptr_t)v.Le & 15) == 0)
+        stencil_row4<comp, typename Pol::coef>(stg, stg + nx, stg + 2 * nx, nx, j, ny, coef_of(v), true, (comp *)v.Le,
+                                               false);
+    else
+        stencil_row<comp, typename Pol::coef>(stg, stg + nx, stg + 2 * nx, nx, j, ny, coef_of(v), true, (comp *)v.Le,
+                                              false);
     SW_TRACE(102);
     const vec *Lpl[KM];
 #pragma unroll
