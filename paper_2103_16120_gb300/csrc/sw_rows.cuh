@@ -237,6 +237,19 @@ __device__ __forceinline__ void ldv4(const T *p, T (&v)[4])
 }
 
 template <class T>
+__device__ __forceinline__ void stv4(T *p, const T (&v)[4])
+{
+    if constexpr (sizeof(T) == 4) {
+        *(float4 *)p = make_float4(v[0], v[1], v[2], v[3]);
+    } else {
+        ((double2 *)p)[0] = make_double2(v[0], v[1]);
+        ((double2 *)p)[1] = make_double2(v[2], v[3]);
+    }
+}
+
+__device__ __forceinline__ bool al16p(const void *p) { return ((uintptr_t)p & 15) == 0; }
+
+template <class T>
 __device__ __forceinline__ void ldw6(const T *rowp, int i0, int nx, T (&v)[6])
 {
     T m[4];

@@ -200,6 +200,35 @@ __device__ void phase_le(const MemberDev<Pol> &M, const MemberCtl &c, const RowV
     const vec *Lpl[KM];
 #pragma unroll
     for (int l = 0; l < KM; ++l) Lpl[l] = v.Lpb + (size_t)phys_slot(c, M.k, l < nd ? l : 0) * v.vstride;
+    // mixed policies: 4 consecutive points per thread, vector reads
+    bool v4 = Pol::kMixed && (nx & 3) == 0 && al16p(v.Le) && al16p(v.r);
+#pragma unroll
+    for (int l = 0; l < KM; ++l) v4 = v4 && al16p(Lpl[l]);
+    if (v4) {
+        for (int i0 = 4 * threadIdx.x; i0 < nx; i0 += 4 * blockDim.x) {
+            vec le4[4], lp4[KM][4];
+            typename Pol::res r4[4];
+            ldv4(v.Le + i0, le4);
+            ldv4(v.r + i0, r4);
+#pragma unroll
+            for (int l = 0; l < KM; ++l)
+                if (l < nd) ldv4(Lpl[l] + i0, lp4[l]);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const acc_t la = (acc_t)le4[u], rv = (acc_t)r4[u];
+                part[0] += la * la;
+                part[1] += rv * la;
+#pragma unroll
+                for (int l = 0; l < KM; ++l) {
+                    if (l < nd) {
+                        part[2 + l] += la * (acc_t)lp4[l][u];
+                        part[2 + KM + l] += rv * (acc_t)lp4[l][u];
+                    }
+                }
+            }
+        }
+        return;
+    }
     constexpr int U = batch_of<comp>();
     for (int i0 = threadIdx.x; i0 < nx; i0 += U * blockDim.x) {
         acc_t la[U], rv[U], lp[KM][U];
@@ -256,6 +285,70 @@ __device__ void phase_ub(const MemberDev<Pol> &M, const MemberCtl &c, const RowV
     const double beta = c.beta;
     const comp beta_c = (comp)beta;
     row_copy_wait();
+    // mixed policies: 4 consecutive points per thread, vector reads and
+    // writes (the FP64 policy keeps the strided loop: the vector form spills
+    // registers in the two-blocks-per-SM instantiation)
+    bool v4 = Pol::kMixed && (nx & 3) == 0 && al16p(v.Le) && al16p(v.r) && al16p(pn) && al16p(Lpn) &&
+              al16p(M.phi + row) && (!v.el || al16p(v.el));
+#pragma unroll
+    for (int l = 0; l < KM; ++l) v4 = v4 && al16p(pl[l]) && al16p(Lpl[l]);
+    if (v4) {
+        for (int i0 = 4 * threadIdx.x; i0 < nx; i0 += 4 * blockDim.x) {
+            comp ev[4];
+            vec le4[4], pv4[KM][4], lp4[KM][4];
+            typename Pol::res r4[4];
+            double ph4[4];
+            if (v.el) {
+                ldv4(v.el + i0, ev);
+            } else {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) ev[u] = q_load(M, M.e, M.e32, esc, j, i0 + u);
+            }
+            ldv4(v.Le + i0, le4);
+            ldv4(v.r + i0, r4);
+            ldv4(phr + i0, ph4);
+#pragma unroll
+            for (int l = 0; l < KM; ++l) {
+                if (l < nd) {
+                    ldv4(pl[l] + i0, pv4[l]);
+                    ldv4(Lpl[l] + i0, lp4[l]);
+                }
+            }
+            vec ps4[4], ls4[4];
+            typename Pol::res rs4[4];
+            double phn[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                comp pv = ev[u], lw = (comp)le4[u];
+#pragma unroll
+                for (int l = 0; l < KM; ++l) {
+                    if (l < nd) {
+                        pv += al[l] * (comp)pv4[l][u];
+                        lw += al[l] * (comp)lp4[l][u];
+                    }
+                }
+                ps4[u] = (vec)pv;
+                ls4[u] = (vec)lw;
+                phn[u] = ph4[u] + beta * (double)ps4[u];
+                if constexpr (Pol::kMixed) rs4[u] = (typename Pol::res)((comp)r4[u] + beta_c * ls4[u]);
+                else rs4[u] = (comp)r4[u] + beta * ls4[u];
+                const acc_t ra = (acc_t)rs4[u], la = (acc_t)ls4[u];
+                part[0] += ra * ra;
+                part[1] += la * la;
+#pragma unroll
+                for (int l = 0; l < KM; ++l)
+                    if (l < nd) part[2 + l] += la * (acc_t)lp4[l][u];
+                sb[pidx(i0 + u)] = stage0_input(M, v, eta, (comp)rs4[u], i0 + u);
+            }
+            stv4(pn + i0, ps4);
+            stv4(Lpn + i0, ls4);
+            stv4(M.phi + row + i0, phn);
+            stv4(v.r + i0, rs4);
+        }
+        SW_TRACE(201);
+        stage0_finish(M, v, j, ws);
+        return;
+    }
     constexpr int U = batch_of<comp>();
     for (int i0 = threadIdx.x; i0 < nx; i0 += U * blockDim.x) {
         // loads of the batch: e, L e, r, p_l, L p_l
