@@ -15,3 +15,6 @@ from .shallow_water import (  # noqa: F401
     EARTH, SWState, synthetic_state, coefficients, rhs_divergence, problem,
     sequence_problem, ensemble_members, random_rhs,
 )
+from .model_state import (  # noqa: F401
+    ModelState, balanced_zonal_state, gravity_mode_state, perturbed_state,
+)
