@@ -22,9 +22,9 @@
  *  - pointers to fields are DEVICE pointers owned by the caller, unless a
  *    comment says "host";
  *  - `stream` is a cudaStream_t (NULL = legacy default stream); every call is
- *    ordered on it, and only sw_gcr_solve / sw_ensemble_solve (to fill their
- *    host-side stats) and sw_elliptic_set_coeffs (to read back the automatic
- *    eta) synchronise it;
+ *    ordered on it, and only sw_gcr_solve, sw_gcr_solve_noalloc,
+ *    sw_ensemble_solve and sw_swe_step with stats (to fill host-side stats)
+ *    synchronise it;
  *  - errors are reported by the returned status only, never by exceptions or
  *    aborts; sw_last_error() gives a message for the calling thread;
  *  - a grid handle must not be used by two host threads at once.
@@ -293,6 +293,80 @@ sw_status sw_gcr_solve_noalloc(sw_grid g, const sw_solve_opts *o, const double *
  * test can make that wait run out without any fault.  sw_debug_barrier(0, 0)
  * restores normal operation. */
 sw_status sw_debug_barrier(int extra_arrivals, double wait_limit_s);
+
+/* ---------------------------------------------------------------------------
+ * Semi-implicit shallow-water time stepping around the solve (Sec. 2.2,
+ * Eqs. 1-10).  A stepper owns the model state on one grid: thickness Phi (m)
+ * and momenta Qx = Phi u, Qy = Phi v (m^2/s), plus the fixed fields of the
+ * forcing (Eqs. 4-5): orography H0, relaxation rate alpha (1/s) and
+ * relaxation target (Qbar_x, Qbar_y).  All fields are device FP64 [ny][nx].
+ *
+ * One step n -> n+1 (all on the stream, FP64 except inside the solves):
+ *  1. winds u, v at n; the advective velocity (a u, a cos(phi) v) at n + 1/2
+ *     by linear extrapolation from n and n-1;
+ *  2. R^n of Eqs. 4-5 and Q^ = Q^n + dt/2 R^n carried over dt by donor-cell
+ *     fluxes (first-order upwind in flux form; MPDATA is not provided), Eq. 6;
+ *  3. for a thickness predictor Phi*: the coefficient fields of Eq. 10 with
+ *     Eq. 7's pressure gradient, Coriolis and relaxation implicit and the
+ *     metric force folded into the Coriolis parameter f + u* tan(phi)/a,
+ *     u* = 2u^n - u^(n-1); they are given to the grid with
+ *     sw_elliptic_set_coeffs;
+ *  4. the right-hand side of the increment solve L(dPhi) = R' with
+ *     R' = div(F^n + F0) - (G/(dt/2)) Phi^n - L(Phi^n), F = (a Qx, a cos(phi) Qy)
+ *     and F0 the explicit part of F at n+1 (face values are means of the two
+ *     cells, no flux through the pole faces); o->tol bounds
+ *     ||L(dPhi) - R'|| / ||R'||, the paper's ||r|| / ||r0|| with first guess
+ *     Phi^n;
+ *  5. steps 3-4 and the solve run twice: with Phi* = Phi^n (increment from
+ *     zero), then with Phi* = Phi^n + that increment (warm-started from it).
+ *     This one outer iteration replaces the explicit transport predictor of
+ *     Eq. 7, which amplifies short zonal waves at the external-mode Courant
+ *     numbers of the pole rows;
+ *  6. Phi^{n+1} = Phi^n + dPhi and the momenta from Eq. 8.
+ * Cell-centred derivatives are centred differences, periodic in longitude,
+ * with the pole row shifted by half a circle beyond each pole.  Winds must
+ * keep the zonal Courant number u dt / (a cos(phi) dlam) below 1 on every
+ * row, pole rows included.
+ * ------------------------------------------------------------------------- */
+typedef struct sw_swe_s *sw_swe;
+
+typedef struct {
+    double dt;        /* time step (s), > 0 */
+    double gravity;   /* g (m s^-2), > 0 */
+    double omega;     /* rotation rate Omega (1/s) */
+} sw_swe_params;
+
+/* Create a stepper on grid g (which must outlive it); allocates about 35
+ * fields of nx*ny doubles on the grid's device.  The grid's coefficients are
+ * replaced at every step. */
+sw_status sw_swe_create(sw_grid g, const sw_swe_params *p, sw_swe *out);
+sw_status sw_swe_destroy(sw_swe m);
+/* Copy a state in (device pointers; H0, alpha, Qbar_x, Qbar_y may be NULL,
+ * meaning zero).  Phi must be positive.  Clears the history: the first step
+ * takes the winds of level n-1 equal to those of level n. */
+sw_status sw_swe_set_state(sw_swe m, const double *Phi, const double *Qx, const double *Qy,
+                           const double *H0, const double *alpha, const double *Qbar_x,
+                           const double *Qbar_y, void *stream);
+/* Set the winds of level n-1 (device, m/s) used by the next step. */
+sw_status sw_swe_set_history(sw_swe m, const double *u_prev, const double *v_prev, void *stream);
+/* Copy the current state out (device pointers; any may be NULL). */
+sw_status sw_swe_get_state(sw_swe m, double *Phi, double *Qx, double *Qy, void *stream);
+/* Steps 1-4 of the next step for the predictor phi_star (device; NULL:
+ * Phi^n), without advancing the state: on return (on the stream) the grid
+ * holds those coefficients.  coeffs: NULL or 7 device pointers (A11, A12,
+ * A21, A22, B1, B2, C; entries may be NULL) that receive copies of the
+ * coefficient fields; rhs: NULL or a device buffer for R'. */
+sw_status sw_swe_explicit(sw_swe m, const double *phi_star, double *const *coeffs, double *rhs,
+                          void *stream);
+/* Advance nsteps (>= 1) steps, two solves each, with options o (FP64 or a
+ * mixed precision; not SW_PC_LEARNED).  Nothing synchronises when stats is
+ * NULL.  Otherwise stats (host, 2 * nsteps entries: each step's predictor and
+ * corrector solves) receives every solve's sw_solve_stats after the call
+ * waits for the stream; a solve that did not converge is reported there (its
+ * status), and the step went on with its last iterate.  Returns argument and
+ * CUDA errors only. */
+sw_status sw_swe_step(sw_swe m, const sw_solve_opts *o, int nsteps, sw_solve_stats *stats,
+                      void *stream);
 
 /* Message describing the last error on the calling host thread. */
 const char *sw_last_error(void);

@@ -7,25 +7,30 @@ One step n -> n+1, in the order of Sec. 2.2, numpy float64 on (ny, nx) arrays:
 1. winds u = Qx/Phi, v = Qy/Phi at level n (Eq. 6 gives the advective
    velocity G(x', y') = (a u, a cos(phi) v)); its value at n + 1/2 by linear
    extrapolation from n and n-1;
-2. the thickness predictor Phi* of Eq. 7: Eq. 1 integrated over dt with that
-   velocity;
-3. the explicit forcing R^n of Eqs. 4-5 (pressure gradient, Coriolis and
+2. the explicit forcing R^n of Eqs. 4-5 (pressure gradient, Coriolis and
    metric force, relaxation), and Q^ = M(Q^n + dt/2 R^n) of Eq. 6;
-4. the coefficient fields of Eq. 10 at n+1 from Phi*, with Coriolis and
-   relaxation implicit and the metric force folded into the Coriolis
-   parameter f~ = f + u* tan(phi)/a, u* the zonal wind extrapolated to n+1
-   (the 2x2 system of Eq. 8 inverted in closed form);
-5. the right-hand side: the trapezoidal Eq. 1 with the momenta of Eq. 8
+3. for a thickness predictor Phi*: the coefficient fields of Eq. 10 at n+1
+   (Eq. 7's pressure gradient, Coriolis and relaxation implicit, the metric
+   force folded into the Coriolis parameter f~ = f + u* tan(phi)/a, u* the
+   zonal wind extrapolated to n+1; the 2x2 system of Eq. 8 inverted in closed
+   form);
+4. the right-hand side: the trapezoidal Eq. 1 with the momenta of Eq. 8
    gives L(Phi^{n+1}) = div(F^n + F0) - (G/delta) Phi^n, F = (a Qx, a cos(phi) Qy)
    the mass flux and F0 its explicit part at n+1; solved for the increment,
-   L(dPhi) = that - L(Phi^n), from zero, so the solver's relative residual is
-   the paper's ||r|| / ||r0|| with first guess Phi^n (Sec. 2.3);
+   L(dPhi) = that - L(Phi^n), so the solver's relative residual is the
+   paper's ||r|| / ||r0|| with first guess Phi^n (Sec. 2.3);
+5. steps 3-4 run twice: first with Phi* = Phi^n (increment from zero), then
+   with Phi* = the Phi^{n+1} of the first solve (increment warm-started from
+   the first one) -- one outer iteration in place of the explicit transport
+   predictor of Eq. 7, which is unstable at the external-mode Courant numbers
+   of the pole rows (the reading and its von Neumann analysis are recorded
+   with the design);
 6. Phi^{n+1} = Phi^n + dPhi and the momenta from Eq. 8.
 
 The explicit transport M is first-order donor-cell upwinding in flux form
 (MPDATA itself is outside this build).  Derivatives at cell centres are
 centred differences, periodic in longitude, with the pole row shifted by half
-a circle as the row beyond a pole.  The flux divergence of step 5 takes face
+a circle as the row beyond a pole.  The flux divergence of step 4 takes face
 values as means of the two adjacent cells and no meridional flux through the
 pole faces, as the operator of Eq. 10 does.
 """
@@ -53,9 +58,11 @@ def _ddphi(f, dphi):
 
 @dataclass
 class StepInfo:
-    ctx: dict                # every intermediate field of the explicit part
-    dphi: np.ndarray         # the increment solved for
-    stats: dict
+    ctx: dict                # every intermediate field of the explicit part (second pass)
+    dphi: np.ndarray         # the increment solved for (second pass)
+    stats: dict              # second solve
+    stats1: dict             # first solve (Phi* = Phi^n)
+    dphi1: np.ndarray        # its increment
 
     @property
     def phi_star(self):
@@ -108,10 +115,10 @@ class Stepper:
         fp[1:-1] = 0.5 * (Fy[:-1] + Fy[1:])
         return (fl - np.roll(fl, 1, axis=1)) / self.dlam + (fp[1:] - fp[:-1]) / self.dphi
 
-    def explicit(self, phi, qx, qy, u_prev=None, v_prev=None) -> dict:
-        """Steps 1-5: everything before the elliptic solve.  u_prev, v_prev:
-        winds at n-1 (None: those of level n).  Returns the intermediate
-        fields by name."""
+    def explicit(self, phi, qx, qy, u_prev=None, v_prev=None, phi_star=None) -> dict:
+        """Steps 1-4: everything before an elliptic solve.  u_prev, v_prev:
+        winds at n-1 (None: those of level n); phi_star: the thickness
+        predictor (None: Phi^n).  Returns the intermediate fields by name."""
         a, g, dt = self.a, self.g, self.dt
         delta = 0.5 * dt
         G = a * a * self.cos
@@ -122,9 +129,9 @@ class Stepper:
         vp = v if v_prev is None else v_prev
         U = a * (1.5 * u - 0.5 * up)
         V = a * self.cos * (1.5 * v - 0.5 * vp)
-        # 2. thickness predictor (Eq. 1 over dt)
-        phi_star = phi - (dt / G) * self._upwind_div(phi, U, V)
-        # 3. explicit forcing at n (Eqs. 4-5) and the transported momenta (Eq. 6)
+        if phi_star is None:
+            phi_star = phi
+        # 2. explicit forcing at n (Eqs. 4-5) and the transported momenta (Eq. 6)
         fn = 2.0 * self.omega * self.sin + u * self.tan / a
         hn = phi + self.h0
         Rx = -(g / (a * self.cos)) * phi * _ddlam(hn, self.dlam) + fn * qy - self.alpha * (qx - self.qbx)
@@ -133,7 +140,7 @@ class Stepper:
         py = qy + delta * Ry
         qhx = px - (dt / G) * self._upwind_div(px, U, V)
         qhy = py - (dt / G) * self._upwind_div(py, U, V)
-        # 4. implicit Coriolis + relaxation at n+1, metric force in f~ (Eq. 8)
+        # 3. implicit Coriolis + relaxation at n+1, metric force in f~ (Eq. 8)
         ustar = 2.0 * u - up
         fs = 2.0 * self.omega * self.sin + ustar * self.tan / a
         c = 1.0 + delta * self.alpha
@@ -158,7 +165,7 @@ class Stepper:
         Y0 = qhy + delta * self.alpha * self.qby - delta * (0.5 * g / a) * phi_star * _ddphi(self.h0, self.dphi)
         F0x = a * (c * X0 + b * Y0) / D
         F0y = a * self.cos * (c * Y0 - b * X0) / D
-        # 5. right-hand side of the increment solve
+        # 4. right-hand side of the increment solve
         prob = Problem(coeffs)
         rhs = self._face_div(a * qx + F0x, a * self.cos * qy + F0y) - coeffs["C"] * phi - prob.operator(phi)
         return dict(u=u, v=v, U=U, V=V, phi_star=phi_star, Rx=Rx, Ry=Ry, qhx=qhx, qhy=qhy, ustar=ustar,
@@ -176,14 +183,17 @@ class Stepper:
         return (c * X + b * Y) / D, (c * Y - b * X) / D
 
     def step(self, phi, qx, qy, u_prev=None, v_prev=None, opts: Opts | None = None):
-        """One step.  Returns (phi1, qx1, qy1, u_n, v_n, StepInfo)."""
-        ctx = self.explicit(phi, qx, qy, u_prev, v_prev)
+        """One step (two solves, step 5).  Returns (phi1, qx1, qy1, u_n, v_n,
+        StepInfo)."""
         if opts is None:
             opts = Opts(tol=1e-12, max_iters=2000)
-        dphi, stats = ctx["problem"].gcr(ctx["rhs"], opts)
+        ctx1 = self.explicit(phi, qx, qy, u_prev, v_prev)
+        d1, st1 = ctx1["problem"].gcr(ctx1["rhs"], opts)
+        ctx = self.explicit(phi, qx, qy, u_prev, v_prev, phi_star=phi + d1)
+        dphi, stats = ctx["problem"].gcr(ctx["rhs"], opts, phi0=d1)
         phi1 = phi + dphi
         qx1, qy1 = self.recover(phi1, ctx)
-        return phi1, qx1, qy1, ctx["u"], ctx["v"], StepInfo(ctx, dphi, stats)
+        return phi1, qx1, qy1, ctx["u"], ctx["v"], StepInfo(ctx, dphi, stats, st1, d1)
 
     def run(self, phi, qx, qy, nsteps: int, opts: Opts | None = None):
         """nsteps steps from a state without history; returns the final state

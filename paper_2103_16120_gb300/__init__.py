@@ -17,7 +17,7 @@ from ._lib import (  # noqa: F401
     SW_ERR_NONFINITE, SW_ERR_TIMEOUT, SW_ERR_INTERNAL,
     SW_PREC_FP64, SW_PREC_MIXED_FP16, SW_PREC_MIXED_BF16, SW_PREC_FP32,
     SW_PC_NONE, SW_PC_DIAG, SW_PC_DIAG_RICHARDSON, SW_PC_SI_RICHARDSON, SW_PC_LEARNED, SW_NOALLOC_SCRATCH_BYTES,
-    SW_MODEL_PARAMS, AdamW,
+    SW_MODEL_PARAMS, AdamW, SweParams,
 )
 
 COEFF_KEYS = ("A11", "A12", "A21", "A22", "B1", "B2", "C")
@@ -302,3 +302,74 @@ def sw_model_target(m: Model, g: Grid, r, e, y, stream=None) -> None:
 
 def sw_debug_barrier(extra_arrivals: int, wait_limit_s: float) -> None:
     _check(load().sw_debug_barrier(int(extra_arrivals), float(wait_limit_s)), "sw_debug_barrier")
+
+
+# ---------------------------------------------------------------------------
+# semi-implicit shallow-water time stepping around the solve (Eqs. 1-10)
+# ---------------------------------------------------------------------------
+class Swe:
+    """Handle of a time stepper on a grid (sw_swe); destroyed with the object.
+    Keeps a reference to the grid, which must outlive it."""
+
+    def __init__(self, g: Grid, dt: float, gravity: float = 9.80616, omega: float = 7.292e-5):
+        self.grid = g
+        self.handle = C.c_void_p()
+        p = SweParams(float(dt), float(gravity), float(omega))
+        _check(load().sw_swe_create(g.handle, C.byref(p), C.byref(self.handle)), "sw_swe_create")
+
+    def __del__(self):
+        if getattr(self, "handle", None) and self.handle.value:
+            try:
+                load().sw_swe_destroy(self.handle)
+            except Exception:
+                pass
+            self.handle = C.c_void_p()
+
+
+def sw_swe_create(g: Grid, dt: float, gravity: float = 9.80616, omega: float = 7.292e-5) -> Swe:
+    return Swe(g, dt, gravity, omega)
+
+
+def sw_swe_set_state(m: Swe, Phi, Qx, Qy, H0=None, alpha=None, Qbar_x=None, Qbar_y=None, stream=None) -> None:
+    import torch
+    shp = (m.grid.ny, m.grid.nx)
+    ptrs = [_ptr(t, torch.float64, shp) for t in (Phi, Qx, Qy, H0, alpha, Qbar_x, Qbar_y)]
+    _check(load().sw_swe_set_state(m.handle, *ptrs, _stream(stream)), "sw_swe_set_state")
+
+
+def sw_swe_set_history(m: Swe, u_prev, v_prev, stream=None) -> None:
+    import torch
+    shp = (m.grid.ny, m.grid.nx)
+    _check(load().sw_swe_set_history(m.handle, _ptr(u_prev, torch.float64, shp), _ptr(v_prev, torch.float64, shp),
+                                     _stream(stream)), "sw_swe_set_history")
+
+
+def sw_swe_get_state(m: Swe, Phi=None, Qx=None, Qy=None, stream=None) -> None:
+    import torch
+    shp = (m.grid.ny, m.grid.nx)
+    ptrs = [_ptr(t, torch.float64, shp) for t in (Phi, Qx, Qy)]
+    _check(load().sw_swe_get_state(m.handle, *ptrs, _stream(stream)), "sw_swe_get_state")
+
+
+def sw_swe_explicit(m: Swe, phi_star=None, coeffs=None, rhs=None, stream=None) -> None:
+    """Steps 1-4 of the next step for the predictor phi_star (None: Phi^n);
+    coeffs: None or 7 tensors (A11..C, entries may be None) receiving the
+    coefficient fields; rhs: None or a tensor for R'."""
+    import torch
+    shp = (m.grid.ny, m.grid.nx)
+    arr = None
+    if coeffs is not None:
+        if len(coeffs) != 7:
+            raise ValueError("coeffs needs 7 entries")
+        arr = (C.c_void_p * 7)(*[None if t is None else _ptr(t, torch.float64, shp).value for t in coeffs])
+    _check(load().sw_swe_explicit(m.handle, _ptr(phi_star, torch.float64, shp), arr,
+                                  _ptr(rhs, torch.float64, shp), _stream(stream)), "sw_swe_explicit")
+
+
+def sw_swe_step(m: Swe, opts: SolveOpts, nsteps: int = 1, want_stats: bool = True, stream=None):
+    """Advance nsteps steps; returns the list of every solve's SolveStats
+    (2 per step: predictor, corrector; synchronising), or None with
+    want_stats=False (nothing synchronises)."""
+    stats = (SolveStats * (2 * int(nsteps)))() if want_stats else None
+    _check(load().sw_swe_step(m.handle, C.byref(opts), int(nsteps), stats, _stream(stream)), "sw_swe_step")
+    return list(stats) if want_stats else None

@@ -27,6 +27,8 @@ EXPORTS = (
     "sw_last_error", "sw_model_create", "sw_model_destroy", "sw_model_set_params", "sw_model_get_params",
     "sw_model_features", "sw_model_forward", "sw_model_loss_grad", "sw_model_train_step", "sw_model_apply",
     "sw_model_target", "sw_ensemble_solve_async", "sw_debug_barrier",
+    "sw_swe_create", "sw_swe_destroy", "sw_swe_set_state", "sw_swe_set_history", "sw_swe_get_state",
+    "sw_swe_explicit", "sw_swe_step",
 )
 SW_MODEL_PARAMS = 158369
 SW_NOALLOC_SCRATCH_BYTES = 16 << 20
@@ -49,6 +51,10 @@ class SolveStats(C.Structure):
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class SweParams(C.Structure):
+    _fields_ = [("dt", C.c_double), ("gravity", C.c_double), ("omega", C.c_double)]
 
 
 class AdamW(C.Structure):
@@ -98,6 +104,13 @@ def load() -> C.CDLL:
     lib.sw_model_apply.argtypes = [vp, vp, vp, vp, vp]
     lib.sw_model_target.argtypes = [vp, vp, vp, vp, vp, vp]
     del fp
+    lib.sw_swe_create.argtypes = [vp, C.POINTER(SweParams), C.POINTER(vp)]
+    lib.sw_swe_destroy.argtypes = [vp]
+    lib.sw_swe_set_state.argtypes = [vp] * 8 + [vp]
+    lib.sw_swe_set_history.argtypes = [vp, vp, vp, vp]
+    lib.sw_swe_get_state.argtypes = [vp, vp, vp, vp, vp]
+    lib.sw_swe_explicit.argtypes = [vp, vp, C.POINTER(vp), vp, vp]
+    lib.sw_swe_step.argtypes = [vp, C.POINTER(SolveOpts), i, C.POINTER(SolveStats), vp]
     lib.sw_last_error.argtypes = []
     lib.sw_last_error.restype = C.c_char_p
     for name in EXPORTS:

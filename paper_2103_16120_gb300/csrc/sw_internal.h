@@ -38,6 +38,13 @@ struct FactorArgs {
     double *gam32, *ec32;                                // per row, of the FP32 factors
 };
 
+// geometry of a grid handle, for translation units outside sw_api.cu
+struct GridGeom {
+    int nx, ny;
+    double radius;
+};
+GridGeom grid_geom(const ::sw_grid_s *g);
+
 cudaError_t launch_faces(const FaceArgs &a, int threads, cudaStream_t s);
 cudaError_t launch_factor(const FactorArgs &a, bool fp64, int threads, cudaStream_t s);
 size_t gcr_smem_bytes(int prec, int max_nx, int k, int cache_const, int cache_state);

@@ -1,0 +1,536 @@
+// sw_swe.cu -- semi-implicit shallow-water time stepping around the elliptic
+// solve (Sec. 2.2, Eqs. 1-10): the explicit part of a step, the right-hand
+// side of the increment solve and the recovery of the momenta, as FP64
+// stencil kernels over the collocated grid, and the C ABI (sw_swe_*) that
+// runs them with the solver.
+//
+// Every kernel takes one cell per thread: blocks of 128 consecutive
+// longitudes of one latitude row (coalesced rows; the four neighbours come
+// from L1/L2), rows strided by gridDim.y.  A step moves about 90 doubles per
+// cell through these kernels (two passes of the coefficient and right-hand
+// side kernels), against about 350 B per cell per iteration of the FP64
+// solve: the two solves dominate whenever they take more than a few
+// iterations.
+#include <cmath>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/sw_elliptic.h"
+#include "sw_internal.h"
+
+namespace sw {
+
+constexpr int SWE_THREADS = 128;
+
+struct Geom {
+    int nx, ny;
+    double a, dlam, dphi, dt, grav, omega;
+    const double *cosr, *sinr, *tanr;   // per latitude row
+};
+
+// centre and its four neighbours; beyond a pole, the pole row half a circle away
+struct Nbr {
+    size_t c, e, w, n, s;
+};
+
+__device__ __forceinline__ Nbr neighbours(int i, int j, int nx, int ny)
+{
+    Nbr r;
+    const size_t row = (size_t)j * nx;
+    const int ih = i + nx / 2 >= nx ? i + nx / 2 - nx : i + nx / 2;
+    r.c = row + i;
+    r.e = row + (i + 1 == nx ? 0 : i + 1);
+    r.w = row + (i == 0 ? nx - 1 : i - 1);
+    r.n = j + 1 < ny ? row + nx + i : row + ih;
+    r.s = j > 0 ? row - nx + i : row + ih;
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// 1. winds at n, advective velocity at n + 1/2, Q + dt/2 R^n (Eqs. 4-5),
+//    and b = dt/2 (f + u* tan(phi)/a) of the implicit Coriolis term
+// ---------------------------------------------------------------------------
+struct ForcingArgs {
+    Geom G;
+    const double *phi, *qx, *qy, *up, *vp, *h0, *alpha, *qbx, *qby;
+    int has_prev;
+    double *U, *V, *psx, *psy, *bb, *un, *vn;
+};
+
+__global__ void __launch_bounds__(SWE_THREADS) k_swe_forcing(ForcingArgs A)
+{
+    const int nx = A.G.nx, ny = A.G.ny;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nx) return;
+    const double a = A.G.a, delta = 0.5 * A.G.dt;
+    for (int j = blockIdx.y; j < ny; j += gridDim.y) {
+        const Nbr q = neighbours(i, j, nx, ny);
+        const double cj = A.G.cosr[j], sj = A.G.sinr[j], tj = A.G.tanr[j];
+        const double ph = A.phi[q.c], qx = A.qx[q.c], qy = A.qy[q.c];
+        const double u = qx / ph, v = qy / ph;
+        const double upv = A.has_prev ? A.up[q.c] : u;
+        const double vpv = A.has_prev ? A.vp[q.c] : v;
+        A.U[q.c] = a * (1.5 * u - 0.5 * upv);
+        A.V[q.c] = a * cj * (1.5 * v - 0.5 * vpv);
+        const double he = A.phi[q.e] + A.h0[q.e], hw = A.phi[q.w] + A.h0[q.w];
+        const double hn = A.phi[q.n] + A.h0[q.n], hs = A.phi[q.s] + A.h0[q.s];
+        const double f = 2.0 * A.G.omega * sj;
+        const double fn = f + u * tj / a;
+        const double al = A.alpha[q.c];
+        const double Rx = -(A.G.grav / (a * cj)) * ph * ((he - hw) / (2.0 * A.G.dlam)) + fn * qy
+                          - al * (qx - A.qbx[q.c]);
+        const double Ry = -(A.G.grav / a) * ph * ((hn - hs) / (2.0 * A.G.dphi)) - fn * qx
+                          - al * (qy - A.qby[q.c]);
+        A.psx[q.c] = qx + delta * Rx;
+        A.psy[q.c] = qy + delta * Ry;
+        const double ustar = 2.0 * u - upv;
+        A.bb[q.c] = delta * (f + ustar * tj / a);
+        A.un[q.c] = u;
+        A.vn[q.c] = v;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 2. donor-cell transport of Q + dt/2 R^n over dt (Eq. 6): face velocity =
+//    mean of the two cells, nothing through the pole faces
+// ---------------------------------------------------------------------------
+struct TransportArgs {
+    Geom G;
+    const double *U, *V, *psx, *psy;
+    double *qhx, *qhy;
+};
+
+__device__ __forceinline__ double donor(double vel, double up, double down)
+{
+    return fmax(vel, 0.0) * up + fmin(vel, 0.0) * down;
+}
+
+__global__ void __launch_bounds__(SWE_THREADS) k_swe_transport(TransportArgs A)
+{
+    const int nx = A.G.nx, ny = A.G.ny;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nx) return;
+    for (int j = blockIdx.y; j < ny; j += gridDim.y) {
+        const Nbr q = neighbours(i, j, nx, ny);
+        const double scale = A.G.dt / (A.G.a * A.G.a * A.G.cosr[j]);
+        const double Uc = A.U[q.c];
+        const double ue = 0.5 * (Uc + A.U[q.e]);
+        const double uw = 0.5 * (A.U[q.w] + Uc);
+        const double Vc = A.V[q.c];
+        const double vn = j + 1 < ny ? 0.5 * (Vc + A.V[q.n]) : 0.0;
+        const double vs = j > 0 ? 0.5 * (A.V[q.s] + Vc) : 0.0;
+        const double *src[2] = {A.psx, A.psy};
+        double *dst[2] = {A.qhx, A.qhy};
+#pragma unroll
+        for (int f = 0; f < 2; ++f) {
+            const double *p = src[f];
+            const double pc = p[q.c];
+            const double fe = donor(ue, pc, p[q.e]);
+            const double fw = donor(uw, p[q.w], pc);
+            const double fnf = j + 1 < ny ? donor(vn, pc, p[q.n]) : 0.0;
+            const double fsf = j > 0 ? donor(vs, p[q.s], pc) : 0.0;
+            const double div = (fe - fw) / A.G.dlam + (fnf - fsf) / A.G.dphi;
+            dst[f][q.c] = pc - scale * div;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 3. coefficients of Eq. 10 from the predictor Phi* = pbase + pinc (Eq. 7;
+//    pinc may be null), the explicit momenta X0, Y0 at n+1 and the mass flux
+//    F^n + F0 (Eq. 8 inverted in closed form)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double pred(const double *base, const double *inc, size_t k)
+{
+    return inc ? base[k] + inc[k] : base[k];
+}
+
+struct CoeffArgs {
+    Geom G;
+    const double *pbase, *pinc, *h0, *alpha, *qbx, *qby, *qhx, *qhy, *bb, *qx, *qy;
+    double *A11, *A12, *A21, *A22, *B1, *B2, *C;
+    double *X0, *Y0, *fsx, *fsy;
+};
+
+__global__ void __launch_bounds__(SWE_THREADS) k_swe_coeffs(CoeffArgs A)
+{
+    const int nx = A.G.nx, ny = A.G.ny;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nx) return;
+    const double a = A.G.a, g = A.G.grav, delta = 0.5 * A.G.dt;
+    for (int j = blockIdx.y; j < ny; j += gridDim.y) {
+        const Nbr q = neighbours(i, j, nx, ny);
+        const double cj = A.G.cosr[j];
+        const double c = 1.0 + delta * A.alpha[q.c];
+        const double b = A.bb[q.c];
+        const double D = c * c + b * b;
+        const double ps = pred(A.pbase, A.pinc, q.c);
+        const double kappa = 0.5 * delta * g * ps;
+        const double dhl = ((pred(A.pbase, A.pinc, q.e) + A.h0[q.e]) - (pred(A.pbase, A.pinc, q.w) + A.h0[q.w]))
+                           / (2.0 * A.G.dlam);
+        const double dhp = ((pred(A.pbase, A.pinc, q.n) + A.h0[q.n]) - (pred(A.pbase, A.pinc, q.s) + A.h0[q.s]))
+                           / (2.0 * A.G.dphi);
+        A.A11[q.c] = kappa * c / (D * cj);
+        A.A12[q.c] = kappa * b / D;
+        A.A21[q.c] = -kappa * b / D;
+        A.A22[q.c] = kappa * c * cj / D;
+        A.B1[q.c] = (0.5 * delta * g / D) * (c * dhl / cj + b * dhp);
+        A.B2[q.c] = (0.5 * delta * g / D) * (c * cj * dhp - b * dhl);
+        A.C[q.c] = (a * a * cj) / delta;
+        const double d0l = (A.h0[q.e] - A.h0[q.w]) / (2.0 * A.G.dlam);
+        const double d0p = (A.h0[q.n] - A.h0[q.s]) / (2.0 * A.G.dphi);
+        const double al = A.alpha[q.c];
+        const double X0 = A.qhx[q.c] + delta * al * A.qbx[q.c] - delta * (0.5 * g / (a * cj)) * ps * d0l;
+        const double Y0 = A.qhy[q.c] + delta * al * A.qby[q.c] - delta * (0.5 * g / a) * ps * d0p;
+        A.X0[q.c] = X0;
+        A.Y0[q.c] = Y0;
+        A.fsx[q.c] = a * A.qx[q.c] + a * (c * X0 + b * Y0) / D;
+        A.fsy[q.c] = a * cj * A.qy[q.c] + a * cj * (c * Y0 - b * X0) / D;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 5. R' = div(F^n + F0) - C Phi^n - L(Phi^n); Lphi holds L(Phi^n) on entry
+//    and R' on return (same cell, read before written)
+// ---------------------------------------------------------------------------
+struct RhsArgs {
+    Geom G;
+    const double *fsx, *fsy, *phi;
+    double *rhs;
+};
+
+__global__ void __launch_bounds__(SWE_THREADS) k_swe_rhs(RhsArgs A)
+{
+    const int nx = A.G.nx, ny = A.G.ny;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nx) return;
+    const double delta = 0.5 * A.G.dt;
+    for (int j = blockIdx.y; j < ny; j += gridDim.y) {
+        const Nbr q = neighbours(i, j, nx, ny);
+        const double xc = A.fsx[q.c], yc = A.fsy[q.c];
+        const double fe = 0.5 * (xc + A.fsx[q.e]);
+        const double fw = 0.5 * (A.fsx[q.w] + xc);
+        const double fn = j + 1 < ny ? 0.5 * (A.fsy[q.n] + yc) : 0.0;
+        const double fs = j > 0 ? 0.5 * (yc + A.fsy[q.s]) : 0.0;
+        const double div = (fe - fw) / A.G.dlam + (fn - fs) / A.G.dphi;
+        const double C = (A.G.a * A.G.a * A.G.cosr[j]) / delta;
+        A.rhs[q.c] = div - C * A.phi[q.c] - A.rhs[q.c];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 6. Phi^{n+1} = Phi^n + dPhi and the momenta of Eq. 8 with the pressure
+//    gradient of Eq. 7
+// ---------------------------------------------------------------------------
+struct RecoverArgs {
+    Geom G;
+    const double *phi, *dphi, *pinc, *h0, *alpha, *bb, *X0, *Y0;   // Phi* = phi + pinc
+    double *phi1, *qx1, *qy1;
+};
+
+__global__ void __launch_bounds__(SWE_THREADS) k_swe_recover(RecoverArgs A)
+{
+    const int nx = A.G.nx, ny = A.G.ny;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nx) return;
+    const double a = A.G.a, g = A.G.grav, delta = 0.5 * A.G.dt;
+    for (int j = blockIdx.y; j < ny; j += gridDim.y) {
+        const Nbr q = neighbours(i, j, nx, ny);
+        const double cj = A.G.cosr[j];
+        const double p1c = A.phi[q.c] + A.dphi[q.c];
+        const double p1e = A.phi[q.e] + A.dphi[q.e], p1w = A.phi[q.w] + A.dphi[q.w];
+        const double p1n = A.phi[q.n] + A.dphi[q.n], p1s = A.phi[q.s] + A.dphi[q.s];
+        const double ps = pred(A.phi, A.pinc, q.c);
+        const double dhl = ((pred(A.phi, A.pinc, q.e) + A.h0[q.e]) - (pred(A.phi, A.pinc, q.w) + A.h0[q.w]))
+                           / (2.0 * A.G.dlam);
+        const double dhp = ((pred(A.phi, A.pinc, q.n) + A.h0[q.n]) - (pred(A.phi, A.pinc, q.s) + A.h0[q.s]))
+                           / (2.0 * A.G.dphi);
+        const double Px = -(0.5 * g / (a * cj)) * (p1c * dhl + ps * ((p1e - p1w) / (2.0 * A.G.dlam)));
+        const double Py = -(0.5 * g / a) * (p1c * dhp + ps * ((p1n - p1s) / (2.0 * A.G.dphi)));
+        const double X = A.X0[q.c] + delta * Px;
+        const double Y = A.Y0[q.c] + delta * Py;
+        const double c = 1.0 + delta * A.alpha[q.c];
+        const double b = A.bb[q.c];
+        const double D = c * c + b * b;
+        A.phi1[q.c] = p1c;
+        A.qx1[q.c] = (c * X + b * Y) / D;
+        A.qy1[q.c] = (c * Y - b * X) / D;
+    }
+}
+
+}  // namespace sw
+
+using namespace sw;
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+enum SweField {
+    F_PHI0, F_PHI1, F_QX0, F_QX1, F_QY0, F_QY1,   // state, double-buffered
+    F_UP, F_VP, F_UN, F_VN,                      // winds of levels n-1 and n
+    F_H0, F_ALPHA, F_QBX, F_QBY,                 // fixed forcing fields
+    F_U, F_V, F_PSX, F_PSY, F_BB,                // step 1
+    F_QHX, F_QHY,                                // step 2
+    F_A11, F_A12, F_A21, F_A22, F_B1, F_B2, F_C, // step 3
+    F_X0, F_Y0, F_FSX, F_FSY,
+    F_RHS, F_DPH1, F_DPHI,                       // right-hand side, first and second increments
+    F_COUNT
+};
+
+struct sw_swe_s {
+    sw_grid grid;
+    int nx, ny, sms;
+    size_t N;
+    sw_swe_params p;
+    double radius;
+    double *mem = nullptr;       // F_COUNT fields, then the three row tables
+    double *f[F_COUNT];
+    double *rows = nullptr;
+    int cur = 0;                 // state buffer holding level n
+    bool has_state = false, has_prev = false;
+    sw_solve_stats *dstats = nullptr;
+    int dstats_n = 0;
+};
+
+namespace {
+
+sw_status swe_cuda(cudaError_t e, const char *where)
+{
+    std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+    return sw::api_fail(e == cudaErrorMemoryAllocation ? SW_ERR_OOM : SW_ERR_CUDA, m.c_str());
+}
+
+#define SWE_CK(call)                                               \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return swe_cuda(e_, #call);         \
+    } while (0)
+
+Geom geom(const sw_swe_s *m)
+{
+    Geom G;
+    G.nx = m->nx; G.ny = m->ny; G.a = m->radius;
+    G.dlam = 2.0 * M_PI / m->nx; G.dphi = M_PI / m->ny;
+    G.dt = m->p.dt; G.grav = m->p.gravity; G.omega = m->p.omega;
+    G.cosr = m->rows; G.sinr = m->rows + m->ny; G.tanr = m->rows + 2 * m->ny;
+    return G;
+}
+
+dim3 swe_grid(const sw_swe_s *m)
+{
+    return dim3((unsigned)((m->nx + SWE_THREADS - 1) / SWE_THREADS), (unsigned)(m->ny < 65535 ? m->ny : 65535));
+}
+
+double *fld(sw_swe_s *m, int k) { return m->f[k]; }
+
+// steps 1-2 of a step: winds, forcing, transported momenta
+sw_status run_forcing(sw_swe m, cudaStream_t s)
+{
+    const Geom G = geom(m);
+    const int c = m->cur;
+    ForcingArgs fa{G, fld(m, F_PHI0 + c), fld(m, F_QX0 + c), fld(m, F_QY0 + c), fld(m, F_UP), fld(m, F_VP),
+                   fld(m, F_H0), fld(m, F_ALPHA), fld(m, F_QBX), fld(m, F_QBY), m->has_prev ? 1 : 0, fld(m, F_U),
+                   fld(m, F_V), fld(m, F_PSX), fld(m, F_PSY), fld(m, F_BB), fld(m, F_UN), fld(m, F_VN)};
+    k_swe_forcing<<<swe_grid(m), SWE_THREADS, 0, s>>>(fa);
+    SWE_CK(cudaGetLastError());
+    TransportArgs ta{G, fld(m, F_U), fld(m, F_V), fld(m, F_PSX), fld(m, F_PSY), fld(m, F_QHX), fld(m, F_QHY)};
+    k_swe_transport<<<swe_grid(m), SWE_THREADS, 0, s>>>(ta);
+    SWE_CK(cudaGetLastError());
+    return SW_OK;
+}
+
+// steps 3-4 for the predictor Phi* = pbase + pinc: coefficients on the grid,
+// R' in F_RHS
+sw_status run_pass(sw_swe m, const double *pbase, const double *pinc, cudaStream_t s)
+{
+    const Geom G = geom(m);
+    const int c = m->cur;
+    const double *phi = fld(m, F_PHI0 + c), *qx = fld(m, F_QX0 + c), *qy = fld(m, F_QY0 + c);
+    CoeffArgs ca{G, pbase, pinc, fld(m, F_H0), fld(m, F_ALPHA), fld(m, F_QBX), fld(m, F_QBY), fld(m, F_QHX),
+                 fld(m, F_QHY), fld(m, F_BB), qx, qy, fld(m, F_A11), fld(m, F_A12), fld(m, F_A21), fld(m, F_A22),
+                 fld(m, F_B1), fld(m, F_B2), fld(m, F_C), fld(m, F_X0), fld(m, F_Y0), fld(m, F_FSX), fld(m, F_FSY)};
+    k_swe_coeffs<<<swe_grid(m), SWE_THREADS, 0, s>>>(ca);
+    SWE_CK(cudaGetLastError());
+    sw_status st = sw_elliptic_set_coeffs(m->grid, fld(m, F_A11), fld(m, F_A12), fld(m, F_A21), fld(m, F_A22),
+                                          fld(m, F_B1), fld(m, F_B2), fld(m, F_C), s);
+    if (st) return st;
+    st = sw_operator_apply(m->grid, SW_PREC_FP64, phi, fld(m, F_RHS), s);
+    if (st) return st;
+    RhsArgs ra{G, fld(m, F_FSX), fld(m, F_FSY), phi, fld(m, F_RHS)};
+    k_swe_rhs<<<swe_grid(m), SWE_THREADS, 0, s>>>(ra);
+    SWE_CK(cudaGetLastError());
+    return SW_OK;
+}
+
+}  // namespace
+
+extern "C" sw_status sw_swe_create(sw_grid g, const sw_swe_params *p, sw_swe *out)
+{
+    if (!out) return sw::api_fail(SW_ERR_INVALID_ARG, "sw_swe_create: out is NULL");
+    *out = nullptr;
+    if (!g || !p) return sw::api_fail(SW_ERR_INVALID_ARG, "sw_swe_create: NULL grid or params");
+    if (!(p->dt > 0.0) || !std::isfinite(p->dt) || !(p->gravity > 0.0) || !std::isfinite(p->gravity) ||
+        !std::isfinite(p->omega))
+        return sw::api_fail(SW_ERR_INVALID_ARG, "sw_swe_create: dt and gravity must be > 0, omega finite");
+    const sw::GridGeom gg = sw::grid_geom(g);
+    sw_swe m = new (std::nothrow) sw_swe_s();
+    if (!m) return sw::api_fail(SW_ERR_OOM, "sw_swe_create: host allocation failed");
+    m->grid = g; m->nx = gg.nx; m->ny = gg.ny; m->radius = gg.radius; m->p = *p;
+    m->N = (size_t)gg.nx * gg.ny;
+    const size_t stride = (m->N + 31) & ~(size_t)31;     // 256-byte aligned fields
+    cudaError_t e = cudaMalloc((void **)&m->mem, (F_COUNT * stride + 3 * (size_t)m->ny) * sizeof(double));
+    if (e != cudaSuccess) {
+        delete m;
+        return swe_cuda(e, "sw_swe_create: cudaMalloc");
+    }
+    for (int k = 0; k < F_COUNT; ++k) m->f[k] = m->mem + k * stride;
+    m->rows = m->mem + F_COUNT * stride;
+    std::vector<double> rows(3 * (size_t)m->ny);
+    const double dphi = M_PI / m->ny;
+    for (int j = 0; j < m->ny; ++j) {
+        const double lat = -0.5 * M_PI + (j + 0.5) * dphi;
+        rows[j] = std::cos(lat);
+        rows[m->ny + j] = std::sin(lat);
+        rows[2 * m->ny + j] = std::sin(lat) / std::cos(lat);
+    }
+    e = cudaMemcpy(m->rows, rows.data(), rows.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(m->mem, 0, F_COUNT * stride * sizeof(double));
+    if (e != cudaSuccess) {
+        cudaFree(m->mem);
+        delete m;
+        return swe_cuda(e, "sw_swe_create: initialise");
+    }
+    *out = m;
+    return SW_OK;
+}
+
+extern "C" sw_status sw_swe_destroy(sw_swe m)
+{
+    if (!m) return SW_OK;
+    cudaFree(m->mem);
+    if (m->dstats) cudaFree(m->dstats);
+    delete m;
+    return SW_OK;
+}
+
+extern "C" sw_status sw_swe_set_state(sw_swe m, const double *Phi, const double *Qx, const double *Qy,
+                                      const double *H0, const double *alpha, const double *Qbar_x,
+                                      const double *Qbar_y, void *stream)
+{
+    if (!m || !Phi || !Qx || !Qy) return sw::api_fail(SW_ERR_INVALID_ARG, "sw_swe_set_state: NULL stepper or state");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t bytes = m->N * sizeof(double);
+    m->cur = 0;
+    SWE_CK(cudaMemcpyAsync(fld(m, F_PHI0), Phi, bytes, cudaMemcpyDeviceToDevice, s));
+    SWE_CK(cudaMemcpyAsync(fld(m, F_QX0), Qx, bytes, cudaMemcpyDeviceToDevice, s));
+    SWE_CK(cudaMemcpyAsync(fld(m, F_QY0), Qy, bytes, cudaMemcpyDeviceToDevice, s));
+    const double *opt[4] = {H0, alpha, Qbar_x, Qbar_y};
+    const int dst[4] = {F_H0, F_ALPHA, F_QBX, F_QBY};
+    for (int k = 0; k < 4; ++k) {
+        if (opt[k]) SWE_CK(cudaMemcpyAsync(fld(m, dst[k]), opt[k], bytes, cudaMemcpyDeviceToDevice, s));
+        else SWE_CK(cudaMemsetAsync(fld(m, dst[k]), 0, bytes, s));
+    }
+    m->has_state = true;
+    m->has_prev = false;
+    return SW_OK;
+}
+
+extern "C" sw_status sw_swe_set_history(sw_swe m, const double *u_prev, const double *v_prev, void *stream)
+{
+    if (!m || !u_prev || !v_prev) return sw::api_fail(SW_ERR_INVALID_ARG, "sw_swe_set_history: NULL argument");
+    if (!m->has_state) return sw::api_fail(SW_ERR_INVALID_ARG, "sw_swe_set_history: no state set");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t bytes = m->N * sizeof(double);
+    SWE_CK(cudaMemcpyAsync(fld(m, F_UP), u_prev, bytes, cudaMemcpyDeviceToDevice, s));
+    SWE_CK(cudaMemcpyAsync(fld(m, F_VP), v_prev, bytes, cudaMemcpyDeviceToDevice, s));
+    m->has_prev = true;
+    return SW_OK;
+}
+
+extern "C" sw_status sw_swe_get_state(sw_swe m, double *Phi, double *Qx, double *Qy, void *stream)
+{
+    if (!m) return sw::api_fail(SW_ERR_INVALID_ARG, "sw_swe_get_state: NULL stepper");
+    if (!m->has_state) return sw::api_fail(SW_ERR_INVALID_ARG, "sw_swe_get_state: no state set");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t bytes = m->N * sizeof(double);
+    double *dst[3] = {Phi, Qx, Qy};
+    const int src[3] = {F_PHI0, F_QX0, F_QY0};
+    for (int k = 0; k < 3; ++k)
+        if (dst[k]) SWE_CK(cudaMemcpyAsync(dst[k], fld(m, src[k] + m->cur), bytes, cudaMemcpyDeviceToDevice, s));
+    return SW_OK;
+}
+
+extern "C" sw_status sw_swe_explicit(sw_swe m, const double *phi_star, double *const *coeffs, double *rhs,
+                                     void *stream)
+{
+    if (!m) return sw::api_fail(SW_ERR_INVALID_ARG, "sw_swe_explicit: NULL stepper");
+    if (!m->has_state) return sw::api_fail(SW_ERR_INVALID_ARG, "sw_swe_explicit: no state set");
+    cudaStream_t s = (cudaStream_t)stream;
+    sw_status st = run_forcing(m, s);
+    if (st) return st;
+    st = run_pass(m, phi_star ? phi_star : fld(m, F_PHI0 + m->cur), nullptr, s);
+    if (st) return st;
+    const size_t bytes = m->N * sizeof(double);
+    if (coeffs)
+        for (int k = 0; k < 7; ++k)
+            if (coeffs[k]) SWE_CK(cudaMemcpyAsync(coeffs[k], fld(m, F_A11 + k), bytes, cudaMemcpyDeviceToDevice, s));
+    if (rhs) SWE_CK(cudaMemcpyAsync(rhs, fld(m, F_RHS), bytes, cudaMemcpyDeviceToDevice, s));
+    return SW_OK;
+}
+
+extern "C" sw_status sw_swe_step(sw_swe m, const sw_solve_opts *o, int nsteps, sw_solve_stats *stats,
+                                 void *stream)
+{
+    if (!m || !o) return sw::api_fail(SW_ERR_INVALID_ARG, "sw_swe_step: NULL stepper or options");
+    if (!m->has_state) return sw::api_fail(SW_ERR_INVALID_ARG, "sw_swe_step: no state set");
+    if (nsteps < 1) return sw::api_fail(SW_ERR_INVALID_ARG, "sw_swe_step: nsteps must be >= 1");
+    if (o->pc == SW_PC_LEARNED) return sw::api_fail(SW_ERR_INVALID_ARG, "sw_swe_step: SW_PC_LEARNED is not supported");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int nsolves = 2 * nsteps;
+    if (stats && m->dstats_n < nsolves) {
+        if (m->dstats) {
+            SWE_CK(cudaStreamSynchronize(s));
+            SWE_CK(cudaFree(m->dstats));
+            m->dstats = nullptr;
+            m->dstats_n = 0;
+        }
+        SWE_CK(cudaMalloc((void **)&m->dstats, (size_t)nsolves * sizeof(sw_solve_stats)));
+        m->dstats_n = nsolves;
+    }
+    const size_t bytes = m->N * sizeof(double);
+    const Geom G = geom(m);
+    const double *R = fld(m, F_RHS);
+    for (int k = 0; k < nsteps; ++k) {
+        const int c = m->cur, n = 1 - c;
+        const double *phi = fld(m, F_PHI0 + c);
+        sw_status st = run_forcing(m, s);
+        if (st) return st;
+        // predictor pass: Phi* = Phi^n, increment from zero
+        st = run_pass(m, phi, nullptr, s);
+        if (st) return st;
+        double *d1 = fld(m, F_DPH1), *d2 = fld(m, F_DPHI);
+        SWE_CK(cudaMemsetAsync(d1, 0, bytes, s));
+        st = sw_ensemble_solve_async(1, &m->grid, o, &R, &d1, stats ? m->dstats + 2 * k : nullptr, s);
+        if (st) return st;
+        // corrector pass: Phi* = Phi^n + dPhi_1, increment warm-started from dPhi_1
+        st = run_pass(m, phi, d1, s);
+        if (st) return st;
+        SWE_CK(cudaMemcpyAsync(d2, d1, bytes, cudaMemcpyDeviceToDevice, s));
+        st = sw_ensemble_solve_async(1, &m->grid, o, &R, &d2, stats ? m->dstats + 2 * k + 1 : nullptr, s);
+        if (st) return st;
+        RecoverArgs ra{G, phi, d2, d1, fld(m, F_H0), fld(m, F_ALPHA), fld(m, F_BB), fld(m, F_X0), fld(m, F_Y0),
+                       fld(m, F_PHI0 + n), fld(m, F_QX0 + n), fld(m, F_QY0 + n)};
+        k_swe_recover<<<swe_grid(m), SWE_THREADS, 0, s>>>(ra);
+        SWE_CK(cudaGetLastError());
+        m->cur = n;
+        double *t = m->f[F_UP]; m->f[F_UP] = m->f[F_UN]; m->f[F_UN] = t;
+        t = m->f[F_VP]; m->f[F_VP] = m->f[F_VN]; m->f[F_VN] = t;
+        m->has_prev = true;
+    }
+    if (stats) {
+        SWE_CK(cudaMemcpyAsync(stats, m->dstats, (size_t)nsolves * sizeof(sw_solve_stats), cudaMemcpyDeviceToHost, s));
+        SWE_CK(cudaStreamSynchronize(s));
+    }
+    return SW_OK;
+}

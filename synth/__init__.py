@@ -16,5 +16,5 @@ from .shallow_water import (  # noqa: F401
     sequence_problem, ensemble_members, random_rhs,
 )
 from .model_state import (  # noqa: F401
-    ModelState, balanced_zonal_state, gravity_mode_state, perturbed_state,
+    ModelState, balanced_zonal_state, gravity_mode_state, perturbed_state, paper_dt,
 )

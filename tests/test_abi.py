@@ -48,6 +48,8 @@ def test_struct_layout_matches_c(tmp_path):
              'printf("%zu %zu\\n", sizeof(sw_solve_opts), sizeof(sw_solve_stats));']
     lines += [f'printf("%zu\\n", offsetof(sw_solve_opts, {f}));' for f in fields_o]
     lines += [f'printf("%zu\\n", offsetof(sw_solve_stats, {f}));' for f in fields_s]
+    lines += ['printf("%zu %zu %zu %zu\\n", sizeof(sw_swe_params), offsetof(sw_swe_params, dt), '
+              'offsetof(sw_swe_params, gravity), offsetof(sw_swe_params, omega));']
     lines += ['printf("%u\\n", (unsigned)SW_NOALLOC_SCRATCH_BYTES);', "return 0;}"]
     prog.write_text("\n".join(lines))
     exe = tmp_path / "layout"
@@ -56,7 +58,9 @@ def test_struct_layout_matches_c(tmp_path):
     assert vals[0] == C.sizeof(SolveOpts) and vals[1] == C.sizeof(SolveStats)
     from paper_2103_16120_gb300._lib import SW_NOALLOC_SCRATCH_BYTES
     assert vals[-1] == SW_NOALLOC_SCRATCH_BYTES
-    offs = vals[2:-1]
+    from paper_2103_16120_gb300._lib import SweParams
+    assert vals[-5:-1] == [C.sizeof(SweParams)] + [getattr(SweParams, f).offset for f, _ in SweParams._fields_]
+    offs = vals[2:-5]
     assert offs[: len(fields_o)] == [getattr(SolveOpts, f).offset for f in fields_o]
     assert offs[len(fields_o):] == [getattr(SolveStats, f).offset for f in fields_s]
 
@@ -76,6 +80,13 @@ def test_defaults_and_argument_checks_without_gpu(lib):
     assert lib.sw_gcr_solve(None, C.byref(o), None, None, None, None) == SW_ERR_INVALID_ARG
     assert lib.sw_ensemble_solve(1, None, C.byref(o), None, None, None, None) == SW_ERR_INVALID_ARG
     assert lib.sw_gcr_solve_noalloc(None, C.byref(o), None, None, None, None) == SW_ERR_INVALID_ARG
+    from paper_2103_16120_gb300._lib import SweParams
+    p = SweParams(600.0, 9.8, 7.292e-5)
+    assert lib.sw_swe_create(None, C.byref(p), C.byref(h)) == SW_ERR_INVALID_ARG
+    assert lib.sw_swe_create(None, None, None) == SW_ERR_INVALID_ARG
+    assert lib.sw_swe_step(None, C.byref(o), 1, None, None) == SW_ERR_INVALID_ARG
+    assert lib.sw_swe_set_state(None, None, None, None, None, None, None, None, None) == SW_ERR_INVALID_ARG
+    assert lib.sw_swe_destroy(None) == 0
 
 
 def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
