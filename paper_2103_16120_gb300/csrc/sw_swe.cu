@@ -23,10 +23,20 @@ namespace sw {
 
 constexpr int SWE_THREADS = 128;
 
+// FP64 arithmetic issues slowly on this GPU (one warp instruction per 64
+// cycles per SM sub-partition; a division is about ten of them), so the
+// per-row factors come from tables made on the host and each cell divides
+// twice per step (1/Phi for the winds, 1/D of the 2x2 system), both in the
+// forcing kernel.
 struct Geom {
     int nx, ny;
-    double a, dlam, dphi, dt, grav, omega;
+    double a, dt, grav, omega;
+    double inv2dlam, inv2dphi, invdlam, invdphi;   // 1/(2 dlam), 1/(2 dphi), 1/dlam, 1/dphi
     const double *cosr, *sinr, *tanr;   // per latitude row
+    const double *invcos;               // 1 / cos(phi_j)
+    const double *Crow;                 // C of Eq. 10: a^2 cos(phi_j) / (dt/2)
+    const double *tscale;               // dt / (a^2 cos(phi_j)): transport over dt
+    const double *gx;                   // g / (a cos(phi_j)): zonal pressure gradient
 };
 
 // centre and its four neighbours; beyond a pole, the pole row half a circle away
@@ -49,13 +59,14 @@ __device__ __forceinline__ Nbr neighbours(int i, int j, int nx, int ny)
 
 // ---------------------------------------------------------------------------
 // 1. winds at n, advective velocity at n + 1/2, Q + dt/2 R^n (Eqs. 4-5),
-//    and b = dt/2 (f + u* tan(phi)/a) of the implicit Coriolis term
+//    b = dt/2 (f + u* tan(phi)/a) of the implicit Coriolis term and 1/D of
+//    the 2x2 system of Eq. 8 (D = c^2 + b^2, c = 1 + dt/2 alpha)
 // ---------------------------------------------------------------------------
 struct ForcingArgs {
     Geom G;
     const double *phi, *qx, *qy, *up, *vp, *h0, *alpha, *qbx, *qby;
     int has_prev;
-    double *U, *V, *psx, *psy, *bb, *un, *vn;
+    double *U, *V, *psx, *psy, *bb, *invD, *un, *vn;
 };
 
 __global__ void __launch_bounds__(SWE_THREADS) k_swe_forcing(ForcingArgs A)
@@ -63,12 +74,13 @@ __global__ void __launch_bounds__(SWE_THREADS) k_swe_forcing(ForcingArgs A)
     const int nx = A.G.nx, ny = A.G.ny;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nx) return;
-    const double a = A.G.a, delta = 0.5 * A.G.dt;
+    const double a = A.G.a, delta = 0.5 * A.G.dt, ga = A.G.grav / a, inva = 1.0 / a;
     for (int j = blockIdx.y; j < ny; j += gridDim.y) {
         const Nbr q = neighbours(i, j, nx, ny);
-        const double cj = A.G.cosr[j], sj = A.G.sinr[j], tj = A.G.tanr[j];
+        const double cj = A.G.cosr[j], sj = A.G.sinr[j], tja = A.G.tanr[j] * inva;
         const double ph = A.phi[q.c], qx = A.qx[q.c], qy = A.qy[q.c];
-        const double u = qx / ph, v = qy / ph;
+        const double rph = 1.0 / ph;
+        const double u = qx * rph, v = qy * rph;
         const double upv = A.has_prev ? A.up[q.c] : u;
         const double vpv = A.has_prev ? A.vp[q.c] : v;
         A.U[q.c] = a * (1.5 * u - 0.5 * upv);
@@ -76,16 +88,17 @@ __global__ void __launch_bounds__(SWE_THREADS) k_swe_forcing(ForcingArgs A)
         const double he = A.phi[q.e] + A.h0[q.e], hw = A.phi[q.w] + A.h0[q.w];
         const double hn = A.phi[q.n] + A.h0[q.n], hs = A.phi[q.s] + A.h0[q.s];
         const double f = 2.0 * A.G.omega * sj;
-        const double fn = f + u * tj / a;
+        const double fn = f + u * tja;
         const double al = A.alpha[q.c];
-        const double Rx = -(A.G.grav / (a * cj)) * ph * ((he - hw) / (2.0 * A.G.dlam)) + fn * qy
-                          - al * (qx - A.qbx[q.c]);
-        const double Ry = -(A.G.grav / a) * ph * ((hn - hs) / (2.0 * A.G.dphi)) - fn * qx
-                          - al * (qy - A.qby[q.c]);
+        const double Rx = -A.G.gx[j] * ph * ((he - hw) * A.G.inv2dlam) + fn * qy - al * (qx - A.qbx[q.c]);
+        const double Ry = -ga * ph * ((hn - hs) * A.G.inv2dphi) - fn * qx - al * (qy - A.qby[q.c]);
         A.psx[q.c] = qx + delta * Rx;
         A.psy[q.c] = qy + delta * Ry;
         const double ustar = 2.0 * u - upv;
-        A.bb[q.c] = delta * (f + ustar * tj / a);
+        const double b = delta * (f + ustar * tja);
+        const double c = 1.0 + delta * al;
+        A.bb[q.c] = b;
+        A.invD[q.c] = 1.0 / (c * c + b * b);
         A.un[q.c] = u;
         A.vn[q.c] = v;
     }
@@ -113,7 +126,7 @@ __global__ void __launch_bounds__(SWE_THREADS) k_swe_transport(TransportArgs A)
     if (i >= nx) return;
     for (int j = blockIdx.y; j < ny; j += gridDim.y) {
         const Nbr q = neighbours(i, j, nx, ny);
-        const double scale = A.G.dt / (A.G.a * A.G.a * A.G.cosr[j]);
+        const double scale = A.G.tscale[j];
         const double Uc = A.U[q.c];
         const double ue = 0.5 * (Uc + A.U[q.e]);
         const double uw = 0.5 * (A.U[q.w] + Uc);
@@ -130,7 +143,7 @@ __global__ void __launch_bounds__(SWE_THREADS) k_swe_transport(TransportArgs A)
             const double fw = donor(uw, p[q.w], pc);
             const double fnf = j + 1 < ny ? donor(vn, pc, p[q.n]) : 0.0;
             const double fsf = j > 0 ? donor(vs, p[q.s], pc) : 0.0;
-            const double div = (fe - fw) / A.G.dlam + (fnf - fsf) / A.G.dphi;
+            const double div = (fe - fw) * A.G.invdlam + (fnf - fsf) * A.G.invdphi;
             dst[f][q.c] = pc - scale * div;
         }
     }
@@ -148,7 +161,7 @@ __device__ __forceinline__ double pred(const double *base, const double *inc, si
 
 struct CoeffArgs {
     Geom G;
-    const double *pbase, *pinc, *h0, *alpha, *qbx, *qby, *qhx, *qhy, *bb, *qx, *qy;
+    const double *pbase, *pinc, *h0, *alpha, *qbx, *qby, *qhx, *qhy, *bb, *invD, *qx, *qy;
     double *A11, *A12, *A21, *A22, *B1, *B2, *C;
     double *X0, *Y0, *fsx, *fsy;
 };
@@ -159,39 +172,41 @@ __global__ void __launch_bounds__(SWE_THREADS) k_swe_coeffs(CoeffArgs A)
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nx) return;
     const double a = A.G.a, g = A.G.grav, delta = 0.5 * A.G.dt;
+    const double hdg = 0.5 * delta * g, hga = 0.5 * g / a;
     for (int j = blockIdx.y; j < ny; j += gridDim.y) {
         const Nbr q = neighbours(i, j, nx, ny);
-        const double cj = A.G.cosr[j];
-        const double c = 1.0 + delta * A.alpha[q.c];
-        const double b = A.bb[q.c];
-        const double D = c * c + b * b;
-        const double ps = pred(A.pbase, A.pinc, q.c);
-        const double kappa = 0.5 * delta * g * ps;
-        const double dhl = ((pred(A.pbase, A.pinc, q.e) + A.h0[q.e]) - (pred(A.pbase, A.pinc, q.w) + A.h0[q.w]))
-                           / (2.0 * A.G.dlam);
-        const double dhp = ((pred(A.pbase, A.pinc, q.n) + A.h0[q.n]) - (pred(A.pbase, A.pinc, q.s) + A.h0[q.s]))
-                           / (2.0 * A.G.dphi);
-        A.A11[q.c] = kappa * c / (D * cj);
-        A.A12[q.c] = kappa * b / D;
-        A.A21[q.c] = -kappa * b / D;
-        A.A22[q.c] = kappa * c * cj / D;
-        A.B1[q.c] = (0.5 * delta * g / D) * (c * dhl / cj + b * dhp);
-        A.B2[q.c] = (0.5 * delta * g / D) * (c * cj * dhp - b * dhl);
-        A.C[q.c] = (a * a * cj) / delta;
-        const double d0l = (A.h0[q.e] - A.h0[q.w]) / (2.0 * A.G.dlam);
-        const double d0p = (A.h0[q.n] - A.h0[q.s]) / (2.0 * A.G.dphi);
+        const double cj = A.G.cosr[j], ic = A.G.invcos[j];
         const double al = A.alpha[q.c];
-        const double X0 = A.qhx[q.c] + delta * al * A.qbx[q.c] - delta * (0.5 * g / (a * cj)) * ps * d0l;
-        const double Y0 = A.qhy[q.c] + delta * al * A.qby[q.c] - delta * (0.5 * g / a) * ps * d0p;
+        const double c = 1.0 + delta * al;
+        const double b = A.bb[q.c];
+        const double iD = A.invD[q.c];
+        const double ps = pred(A.pbase, A.pinc, q.c);
+        const double kappa = hdg * ps;
+        const double dhl = ((pred(A.pbase, A.pinc, q.e) + A.h0[q.e]) - (pred(A.pbase, A.pinc, q.w) + A.h0[q.w]))
+                           * A.G.inv2dlam;
+        const double dhp = ((pred(A.pbase, A.pinc, q.n) + A.h0[q.n]) - (pred(A.pbase, A.pinc, q.s) + A.h0[q.s]))
+                           * A.G.inv2dphi;
+        const double kci = kappa * c * iD, kbi = kappa * b * iD, hgi = hdg * iD;
+        A.A11[q.c] = kci * ic;
+        A.A12[q.c] = kbi;
+        A.A21[q.c] = -kbi;
+        A.A22[q.c] = kci * cj;
+        A.B1[q.c] = hgi * (c * dhl * ic + b * dhp);
+        A.B2[q.c] = hgi * (c * cj * dhp - b * dhl);
+        A.C[q.c] = A.G.Crow[j];
+        const double d0l = (A.h0[q.e] - A.h0[q.w]) * A.G.inv2dlam;
+        const double d0p = (A.h0[q.n] - A.h0[q.s]) * A.G.inv2dphi;
+        const double X0 = A.qhx[q.c] + delta * al * A.qbx[q.c] - delta * (0.5 * A.G.gx[j]) * ps * d0l;
+        const double Y0 = A.qhy[q.c] + delta * al * A.qby[q.c] - delta * hga * ps * d0p;
         A.X0[q.c] = X0;
         A.Y0[q.c] = Y0;
-        A.fsx[q.c] = a * A.qx[q.c] + a * (c * X0 + b * Y0) / D;
-        A.fsy[q.c] = a * cj * A.qy[q.c] + a * cj * (c * Y0 - b * X0) / D;
+        A.fsx[q.c] = a * A.qx[q.c] + a * (c * X0 + b * Y0) * iD;
+        A.fsy[q.c] = a * cj * A.qy[q.c] + a * cj * (c * Y0 - b * X0) * iD;
     }
 }
 
 // ---------------------------------------------------------------------------
-// 5. R' = div(F^n + F0) - C Phi^n - L(Phi^n); Lphi holds L(Phi^n) on entry
+// 4. R' = div(F^n + F0) - C Phi^n - L(Phi^n); rhs holds L(Phi^n) on entry
 //    and R' on return (same cell, read before written)
 // ---------------------------------------------------------------------------
 struct RhsArgs {
@@ -205,7 +220,6 @@ __global__ void __launch_bounds__(SWE_THREADS) k_swe_rhs(RhsArgs A)
     const int nx = A.G.nx, ny = A.G.ny;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nx) return;
-    const double delta = 0.5 * A.G.dt;
     for (int j = blockIdx.y; j < ny; j += gridDim.y) {
         const Nbr q = neighbours(i, j, nx, ny);
         const double xc = A.fsx[q.c], yc = A.fsy[q.c];
@@ -213,9 +227,8 @@ __global__ void __launch_bounds__(SWE_THREADS) k_swe_rhs(RhsArgs A)
         const double fw = 0.5 * (A.fsx[q.w] + xc);
         const double fn = j + 1 < ny ? 0.5 * (A.fsy[q.n] + yc) : 0.0;
         const double fs = j > 0 ? 0.5 * (yc + A.fsy[q.s]) : 0.0;
-        const double div = (fe - fw) / A.G.dlam + (fn - fs) / A.G.dphi;
-        const double C = (A.G.a * A.G.a * A.G.cosr[j]) / delta;
-        A.rhs[q.c] = div - C * A.phi[q.c] - A.rhs[q.c];
+        const double div = (fe - fw) * A.G.invdlam + (fn - fs) * A.G.invdphi;
+        A.rhs[q.c] = div - A.G.Crow[j] * A.phi[q.c] - A.rhs[q.c];
     }
 }
 
@@ -225,7 +238,7 @@ __global__ void __launch_bounds__(SWE_THREADS) k_swe_rhs(RhsArgs A)
 // ---------------------------------------------------------------------------
 struct RecoverArgs {
     Geom G;
-    const double *phi, *dphi, *pinc, *h0, *alpha, *bb, *X0, *Y0;   // Phi* = phi + pinc
+    const double *phi, *dphi, *pinc, *h0, *alpha, *bb, *invD, *X0, *Y0;   // Phi* = phi + pinc
     double *phi1, *qx1, *qy1;
 };
 
@@ -234,28 +247,27 @@ __global__ void __launch_bounds__(SWE_THREADS) k_swe_recover(RecoverArgs A)
     const int nx = A.G.nx, ny = A.G.ny;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nx) return;
-    const double a = A.G.a, g = A.G.grav, delta = 0.5 * A.G.dt;
+    const double delta = 0.5 * A.G.dt, hga = 0.5 * A.G.grav / A.G.a;
     for (int j = blockIdx.y; j < ny; j += gridDim.y) {
         const Nbr q = neighbours(i, j, nx, ny);
-        const double cj = A.G.cosr[j];
         const double p1c = A.phi[q.c] + A.dphi[q.c];
         const double p1e = A.phi[q.e] + A.dphi[q.e], p1w = A.phi[q.w] + A.dphi[q.w];
         const double p1n = A.phi[q.n] + A.dphi[q.n], p1s = A.phi[q.s] + A.dphi[q.s];
         const double ps = pred(A.phi, A.pinc, q.c);
         const double dhl = ((pred(A.phi, A.pinc, q.e) + A.h0[q.e]) - (pred(A.phi, A.pinc, q.w) + A.h0[q.w]))
-                           / (2.0 * A.G.dlam);
+                           * A.G.inv2dlam;
         const double dhp = ((pred(A.phi, A.pinc, q.n) + A.h0[q.n]) - (pred(A.phi, A.pinc, q.s) + A.h0[q.s]))
-                           / (2.0 * A.G.dphi);
-        const double Px = -(0.5 * g / (a * cj)) * (p1c * dhl + ps * ((p1e - p1w) / (2.0 * A.G.dlam)));
-        const double Py = -(0.5 * g / a) * (p1c * dhp + ps * ((p1n - p1s) / (2.0 * A.G.dphi)));
+                           * A.G.inv2dphi;
+        const double Px = -(0.5 * A.G.gx[j]) * (p1c * dhl + ps * ((p1e - p1w) * A.G.inv2dlam));
+        const double Py = -hga * (p1c * dhp + ps * ((p1n - p1s) * A.G.inv2dphi));
         const double X = A.X0[q.c] + delta * Px;
         const double Y = A.Y0[q.c] + delta * Py;
         const double c = 1.0 + delta * A.alpha[q.c];
         const double b = A.bb[q.c];
-        const double D = c * c + b * b;
+        const double iD = A.invD[q.c];
         A.phi1[q.c] = p1c;
-        A.qx1[q.c] = (c * X + b * Y) / D;
-        A.qy1[q.c] = (c * Y - b * X) / D;
+        A.qx1[q.c] = (c * X + b * Y) * iD;
+        A.qy1[q.c] = (c * Y - b * X) * iD;
     }
 }
 
@@ -270,7 +282,7 @@ enum SweField {
     F_PHI0, F_PHI1, F_QX0, F_QX1, F_QY0, F_QY1,   // state, double-buffered
     F_UP, F_VP, F_UN, F_VN,                      // winds of levels n-1 and n
     F_H0, F_ALPHA, F_QBX, F_QBY,                 // fixed forcing fields
-    F_U, F_V, F_PSX, F_PSY, F_BB,                // step 1
+    F_U, F_V, F_PSX, F_PSY, F_BB, F_IND,         // step 1
     F_QHX, F_QHY,                                // step 2
     F_A11, F_A12, F_A21, F_A22, F_B1, F_B2, F_C, // step 3
     F_X0, F_Y0, F_FSX, F_FSY,
@@ -307,13 +319,20 @@ sw_status swe_cuda(cudaError_t e, const char *where)
         if (e_ != cudaSuccess) return swe_cuda(e_, #call);         \
     } while (0)
 
+constexpr int NROWTAB = 7;   // cos, sin, tan, 1/cos, C, dt/(a^2 cos), g/(a cos)
+
 Geom geom(const sw_swe_s *m)
 {
     Geom G;
+    const double dlam = 2.0 * M_PI / m->nx, dphi = M_PI / m->ny;
     G.nx = m->nx; G.ny = m->ny; G.a = m->radius;
-    G.dlam = 2.0 * M_PI / m->nx; G.dphi = M_PI / m->ny;
     G.dt = m->p.dt; G.grav = m->p.gravity; G.omega = m->p.omega;
-    G.cosr = m->rows; G.sinr = m->rows + m->ny; G.tanr = m->rows + 2 * m->ny;
+    G.inv2dlam = 1.0 / (2.0 * dlam); G.inv2dphi = 1.0 / (2.0 * dphi);
+    G.invdlam = 1.0 / dlam; G.invdphi = 1.0 / dphi;
+    const double *r = m->rows;
+    const size_t ny = (size_t)m->ny;
+    G.cosr = r; G.sinr = r + ny; G.tanr = r + 2 * ny; G.invcos = r + 3 * ny;
+    G.Crow = r + 4 * ny; G.tscale = r + 5 * ny; G.gx = r + 6 * ny;
     return G;
 }
 
@@ -331,7 +350,8 @@ sw_status run_forcing(sw_swe m, cudaStream_t s)
     const int c = m->cur;
     ForcingArgs fa{G, fld(m, F_PHI0 + c), fld(m, F_QX0 + c), fld(m, F_QY0 + c), fld(m, F_UP), fld(m, F_VP),
                    fld(m, F_H0), fld(m, F_ALPHA), fld(m, F_QBX), fld(m, F_QBY), m->has_prev ? 1 : 0, fld(m, F_U),
-                   fld(m, F_V), fld(m, F_PSX), fld(m, F_PSY), fld(m, F_BB), fld(m, F_UN), fld(m, F_VN)};
+                   fld(m, F_V), fld(m, F_PSX), fld(m, F_PSY), fld(m, F_BB), fld(m, F_IND), fld(m, F_UN),
+                   fld(m, F_VN)};
     k_swe_forcing<<<swe_grid(m), SWE_THREADS, 0, s>>>(fa);
     SWE_CK(cudaGetLastError());
     TransportArgs ta{G, fld(m, F_U), fld(m, F_V), fld(m, F_PSX), fld(m, F_PSY), fld(m, F_QHX), fld(m, F_QHY)};
@@ -348,7 +368,7 @@ sw_status run_pass(sw_swe m, const double *pbase, const double *pinc, cudaStream
     const int c = m->cur;
     const double *phi = fld(m, F_PHI0 + c), *qx = fld(m, F_QX0 + c), *qy = fld(m, F_QY0 + c);
     CoeffArgs ca{G, pbase, pinc, fld(m, F_H0), fld(m, F_ALPHA), fld(m, F_QBX), fld(m, F_QBY), fld(m, F_QHX),
-                 fld(m, F_QHY), fld(m, F_BB), qx, qy, fld(m, F_A11), fld(m, F_A12), fld(m, F_A21), fld(m, F_A22),
+                 fld(m, F_QHY), fld(m, F_BB), fld(m, F_IND), qx, qy, fld(m, F_A11), fld(m, F_A12), fld(m, F_A21), fld(m, F_A22),
                  fld(m, F_B1), fld(m, F_B2), fld(m, F_C), fld(m, F_X0), fld(m, F_Y0), fld(m, F_FSX), fld(m, F_FSY)};
     k_swe_coeffs<<<swe_grid(m), SWE_THREADS, 0, s>>>(ca);
     SWE_CK(cudaGetLastError());
@@ -379,20 +399,26 @@ extern "C" sw_status sw_swe_create(sw_grid g, const sw_swe_params *p, sw_swe *ou
     m->grid = g; m->nx = gg.nx; m->ny = gg.ny; m->radius = gg.radius; m->p = *p;
     m->N = (size_t)gg.nx * gg.ny;
     const size_t stride = (m->N + 31) & ~(size_t)31;     // 256-byte aligned fields
-    cudaError_t e = cudaMalloc((void **)&m->mem, (F_COUNT * stride + 3 * (size_t)m->ny) * sizeof(double));
+    cudaError_t e = cudaMalloc((void **)&m->mem, (F_COUNT * stride + NROWTAB * (size_t)m->ny) * sizeof(double));
     if (e != cudaSuccess) {
         delete m;
         return swe_cuda(e, "sw_swe_create: cudaMalloc");
     }
     for (int k = 0; k < F_COUNT; ++k) m->f[k] = m->mem + k * stride;
     m->rows = m->mem + F_COUNT * stride;
-    std::vector<double> rows(3 * (size_t)m->ny);
-    const double dphi = M_PI / m->ny;
-    for (int j = 0; j < m->ny; ++j) {
+    const size_t ny = (size_t)m->ny;
+    std::vector<double> rows(NROWTAB * ny);
+    const double dphi = M_PI / m->ny, a = m->radius, delta = 0.5 * p->dt;
+    for (size_t j = 0; j < ny; ++j) {
         const double lat = -0.5 * M_PI + (j + 0.5) * dphi;
-        rows[j] = std::cos(lat);
-        rows[m->ny + j] = std::sin(lat);
-        rows[2 * m->ny + j] = std::sin(lat) / std::cos(lat);
+        const double c = std::cos(lat), sn = std::sin(lat);
+        rows[j] = c;
+        rows[ny + j] = sn;
+        rows[2 * ny + j] = sn / c;
+        rows[3 * ny + j] = 1.0 / c;
+        rows[4 * ny + j] = (a * a * c) / delta;
+        rows[5 * ny + j] = p->dt / (a * a * c);
+        rows[6 * ny + j] = p->gravity / (a * c);
     }
     e = cudaMemcpy(m->rows, rows.data(), rows.size() * sizeof(double), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(m->mem, 0, F_COUNT * stride * sizeof(double));
@@ -519,7 +545,8 @@ extern "C" sw_status sw_swe_step(sw_swe m, const sw_solve_opts *o, int nsteps, s
         SWE_CK(cudaMemcpyAsync(d2, d1, bytes, cudaMemcpyDeviceToDevice, s));
         st = sw_ensemble_solve_async(1, &m->grid, o, &R, &d2, stats ? m->dstats + 2 * k + 1 : nullptr, s);
         if (st) return st;
-        RecoverArgs ra{G, phi, d2, d1, fld(m, F_H0), fld(m, F_ALPHA), fld(m, F_BB), fld(m, F_X0), fld(m, F_Y0),
+        RecoverArgs ra{G, phi, d2, d1, fld(m, F_H0), fld(m, F_ALPHA), fld(m, F_BB), fld(m, F_IND), fld(m, F_X0),
+                       fld(m, F_Y0),
                        fld(m, F_PHI0 + n), fld(m, F_QX0 + n), fld(m, F_QY0 + n)};
         k_swe_recover<<<swe_grid(m), SWE_THREADS, 0, s>>>(ra);
         SWE_CK(cudaGetLastError());
