@@ -317,8 +317,11 @@ sw_status sw_debug_barrier(int extra_arrivals, double wait_limit_s);
  *     cells, no flux through the pole faces); o->tol bounds
  *     ||L(dPhi) - R'|| / ||R'||, the paper's ||r|| / ||r0|| with first guess
  *     Phi^n;
- *  5. steps 3-4 and the solve run twice: with Phi* = Phi^n (increment from
- *     zero), then with Phi* = Phi^n + that increment (warm-started from it).
+ *  5. steps 3-4 and the solve run twice: with Phi* = Phi^n, then with
+ *     Phi* = Phi^n + that increment (warm-started from it).  The first solve
+ *     starts from the increment extrapolated from the last two steps
+ *     (2 dPhi^(n-1) - dPhi^(n-2); after sw_swe_set_state: zero, then the last
+ *     increment), which changes its iteration count, not its tolerance.
  *     This one outer iteration replaces the explicit transport predictor of
  *     Eq. 7, which amplifies short zonal waves at the external-mode Courant
  *     numbers of the pole rows;

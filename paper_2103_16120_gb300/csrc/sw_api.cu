@@ -70,7 +70,7 @@ constexpr int RING = 4;
 
 static size_t ring_slot_bytes() { return ((sizeof(SolverBlock::dev) + 255) & ~(size_t)255) + sizeof(EnsDesc); }
 
-GridGeom sw::grid_geom(const sw_grid_s *g) { return GridGeom{g->nx, g->ny, g->radius}; }
+GridGeom sw::grid_geom(const sw_grid_s *g) { return GridGeom{g->nx, g->ny, g->sms > 0 ? g->sms : 1, g->radius}; }
 
 GridView sw::grid_view(const sw_grid_s *g)
 {

@@ -40,7 +40,7 @@ struct FactorArgs {
 
 // geometry of a grid handle, for translation units outside sw_api.cu
 struct GridGeom {
-    int nx, ny;
+    int nx, ny, sms;
     double radius;
 };
 GridGeom grid_geom(const ::sw_grid_s *g);

@@ -271,6 +271,16 @@ __global__ void __launch_bounds__(SWE_THREADS) k_swe_recover(RecoverArgs A)
     }
 }
 
+// ---------------------------------------------------------------------------
+// first guess of the predictor solve: the increment extrapolated from the
+// last two steps, 2 dPhi^(n-1) - dPhi^(n-2)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_swe_guess(size_t n, const double *d1, const double *d2, double *out)
+{
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
+        out[k] = 2.0 * d1[k] - d2[k];
+}
+
 }  // namespace sw
 
 using namespace sw;
@@ -287,6 +297,7 @@ enum SweField {
     F_A11, F_A12, F_A21, F_A22, F_B1, F_B2, F_C, // step 3
     F_X0, F_Y0, F_FSX, F_FSY,
     F_RHS, F_DPH1, F_DPHI,                       // right-hand side, first and second increments
+    F_DH1, F_DH2,                                // final increments of the last two steps
     F_COUNT
 };
 
@@ -301,6 +312,7 @@ struct sw_swe_s {
     double *rows = nullptr;
     int cur = 0;                 // state buffer holding level n
     bool has_state = false, has_prev = false;
+    int n_dhist = 0;             // final increments kept from earlier steps (0..2)
     sw_solve_stats *dstats = nullptr;
     int dstats_n = 0;
 };
@@ -396,7 +408,7 @@ extern "C" sw_status sw_swe_create(sw_grid g, const sw_swe_params *p, sw_swe *ou
     const sw::GridGeom gg = sw::grid_geom(g);
     sw_swe m = new (std::nothrow) sw_swe_s();
     if (!m) return sw::api_fail(SW_ERR_OOM, "sw_swe_create: host allocation failed");
-    m->grid = g; m->nx = gg.nx; m->ny = gg.ny; m->radius = gg.radius; m->p = *p;
+    m->grid = g; m->nx = gg.nx; m->ny = gg.ny; m->sms = gg.sms; m->radius = gg.radius; m->p = *p;
     m->N = (size_t)gg.nx * gg.ny;
     const size_t stride = (m->N + 31) & ~(size_t)31;     // 256-byte aligned fields
     cudaError_t e = cudaMalloc((void **)&m->mem, (F_COUNT * stride + NROWTAB * (size_t)m->ny) * sizeof(double));
@@ -459,6 +471,7 @@ extern "C" sw_status sw_swe_set_state(sw_swe m, const double *Phi, const double 
     }
     m->has_state = true;
     m->has_prev = false;
+    m->n_dhist = 0;
     return SW_OK;
 }
 
@@ -535,8 +548,16 @@ extern "C" sw_status sw_swe_step(sw_swe m, const sw_solve_opts *o, int nsteps, s
         // predictor pass: Phi* = Phi^n, increment from zero
         st = run_pass(m, phi, nullptr, s);
         if (st) return st;
+        // first guess: the increment extrapolated from the last two steps
         double *d1 = fld(m, F_DPH1), *d2 = fld(m, F_DPHI);
-        SWE_CK(cudaMemsetAsync(d1, 0, bytes, s));
+        if (m->n_dhist >= 2) {
+            k_swe_guess<<<m->sms * 4, 256, 0, s>>>(m->N, fld(m, F_DH1), fld(m, F_DH2), d1);
+            SWE_CK(cudaGetLastError());
+        } else if (m->n_dhist == 1) {
+            SWE_CK(cudaMemcpyAsync(d1, fld(m, F_DH1), bytes, cudaMemcpyDeviceToDevice, s));
+        } else {
+            SWE_CK(cudaMemsetAsync(d1, 0, bytes, s));
+        }
         st = sw_ensemble_solve_async(1, &m->grid, o, &R, &d1, stats ? m->dstats + 2 * k : nullptr, s);
         if (st) return st;
         // corrector pass: Phi* = Phi^n + dPhi_1, increment warm-started from dPhi_1
@@ -551,6 +572,12 @@ extern "C" sw_status sw_swe_step(sw_swe m, const sw_solve_opts *o, int nsteps, s
         k_swe_recover<<<swe_grid(m), SWE_THREADS, 0, s>>>(ra);
         SWE_CK(cudaGetLastError());
         m->cur = n;
+        // the applied increment becomes the newest history entry (pointer rotation)
+        double *h2 = m->f[F_DH2];
+        m->f[F_DH2] = m->f[F_DH1];
+        m->f[F_DH1] = m->f[F_DPHI];
+        m->f[F_DPHI] = h2;
+        if (m->n_dhist < 2) ++m->n_dhist;
         double *t = m->f[F_UP]; m->f[F_UP] = m->f[F_UN]; m->f[F_UN] = t;
         t = m->f[F_VP]; m->f[F_VP] = m->f[F_VN]; m->f[F_VN] = t;
         m->has_prev = true;

@@ -163,6 +163,9 @@ def test_bench_size_step_and_mass_bound():
     nsteps = 6
     stats = sw.sw_swe_step(m, sw.sw_solve_opts_default(prec=sw.SW_PREC_MIXED_FP16, tol=1e-8), nsteps)
     assert all(x.converged == 1 for x in stats)
+    # from the third step on, the predictor starts from the extrapolated increment
+    pred = [x.iterations for x in stats[0::2]]
+    assert np.mean(pred[2:]) < pred[0]
     gp2, _, _ = state(m)
     # the corrector's increment is the one applied
     bound = sum(math.sqrt(nx * ny) * x.true_rel_residual * x.R_norm for x in stats[1::2]) * (0.5 * dt) / A ** 2
