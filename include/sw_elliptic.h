@@ -192,10 +192,12 @@ sw_status sw_ensemble_solve(int n, const sw_grid *grids, const sw_solve_opts *o,
  * slots, and a call waits on the host only while the stream is four calls
  * behind.  Nothing is allocated once each grid's workspace exists, i.e.
  * after one solve with the same precision and k (or an attached workspace),
- * so the call can then be recorded in a CUDA graph and replayed.  A recorded
- * call stages into a slot of its own, which replays read; it stays valid
- * until the grid's next recorded sw_ensemble_solve_async.  Not for
- * SW_PC_LEARNED. */
+ * so the call can then be recorded in a CUDA graph and replayed.  With one
+ * member (n = 1) the descriptors travel as kernel parameters, with no host
+ * staging and no copies, and a recorded call keeps them for the graph's
+ * lifetime.  With more, a recorded call stages into a slot of its own, which
+ * replays read; it stays valid until the grid's next recorded
+ * sw_ensemble_solve_async.  Not for SW_PC_LEARNED. */
 sw_status sw_ensemble_solve_async(int n, const sw_grid *grids, const sw_solve_opts *o,
                                   const double *const *R, double *const *phi,
                                   sw_solve_stats *stats_dev, void *stream);

@@ -319,7 +319,10 @@ extern "C" sw_status sw_elliptic_set_coeffs(sw_grid g, const double *A11, const 
     a.ax = g->ax; a.cx = g->cx; a.bx = g->bx; a.ay = g->ay; a.cy = g->cy; a.by = g->by; a.C64 = g->C; a.diag = g->diag;
     a.wax = g->wax; a.wcx = g->wcx; a.wbx = g->wbx; a.way = g->way; a.wcy = g->wcy; a.wby = g->wby; a.wC = g->wC;
     a.wdiag = g->wdiag; a.rowmax = g->rowmax;
-    CK(launch_faces(a, row_threads(g->nx), s));
+    // k_faces is latency-bound with one block per row: as many threads as the row
+    // has points, up to the block limit (the scans of k_factor need fewer)
+    const int fthreads = g->nx < MAX_THREADS ? ((g->nx + 31) / 32) * 32 : MAX_THREADS;
+    CK(launch_faces(a, fthreads, s));
     sw_status st = refactor(g, s);
     if (st) return st;
     g->has_coeffs = true;
@@ -839,6 +842,49 @@ extern "C" sw_status sw_gcr_solve_noalloc(sw_grid g, const sw_solve_opts *o, con
 
 // ---------------------------------------------------------------------------
 // ensemble solve without host synchronisation
+// one member: its descriptor and the launch descriptor go to the device as
+// kernel parameters of k_init_one (no host staging, no copies; a graph capture
+// records them by value)
+static sw_status solve_one_async(sw_grid g, const sw_solve_opts *o, const double *R, double *phi,
+                                 sw_solve_stats *stats_dev, int max_nx, cudaStream_t s)
+{
+    sw_status st;
+    if (o->eta > 0.0 && o->eta != g->eta_explicit) {
+        g->eta_explicit = o->eta;
+        if ((st = refactor(g, s))) return st;
+    }
+    if ((st = ensure_ws(g, o->prec, o->k))) return st;
+    if (o->prec == SW_PREC_FP64 && (st = ensure_f64(g, s))) return st;
+    InitOneArgs a;
+    std::memset(&a, 0, sizeof(a));
+    if (o->prec == SW_PREC_FP64) {
+        MemberDev<PolFP64> M;
+        fill_member<PolFP64>(g, o, R, phi, M);
+        std::memcpy(a.mdev, &M, sizeof(M));
+    } else if (o->prec == SW_PREC_MIXED_FP16) {
+        MemberDev<PolF16> M;
+        fill_member<PolF16>(g, o, R, phi, M);
+        std::memcpy(a.mdev, &M, sizeof(M));
+    } else {
+        MemberDev<PolBF16> M;
+        fill_member<PolBF16>(g, o, R, phi, M);
+        std::memcpy(a.mdev, &M, sizeof(M));
+    }
+    if (o->res_history) CK(launch_fill(o->res_history, (size_t)o->max_iters + 1, NAN, s));
+    Plan P;
+    if ((st = plan_launch(1, &g, o, max_nx, P))) return st;
+    a.blk = g->blk;
+    a.desc = g->desc;
+    a.stats = stats_dev;
+    a.grid = P.grid;
+    a.nb0 = P.nb[0];
+    a.cache_const = P.cc;
+    a.cache_state = P.cs;
+    CK(launch_init_one(a, s));
+    CK(launch_gcr(o->prec, o->k, P.minb, g->desc, P.grid, max_nx, P.threads, P.smem, s));
+    return SW_OK;
+}
+
 // ---------------------------------------------------------------------------
 extern "C" sw_status sw_ensemble_solve_async(int n, const sw_grid *grids, const sw_solve_opts *o,
                                              const double *const *R, double *const *phi,
@@ -852,6 +898,7 @@ extern "C" sw_status sw_ensemble_solve_async(int n, const sw_grid *grids, const 
     int max_nx = 0;
     if ((st = check_members(n, grids, o, R, phi, max_nx))) return st;
     cudaStream_t s = (cudaStream_t)stream;
+    if (n == 1) return solve_one_async(grids[0], o, R[0], phi[0], stats_dev, max_nx, s);
     // host staging: a recorded call uses each grid's dedicated slot, which a
     // graph replay reads; otherwise the next ring slot, once the copies of
     // its previous use have run

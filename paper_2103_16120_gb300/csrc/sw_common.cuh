@@ -151,6 +151,16 @@ struct alignas(256) SolverBlock {
     GlobalCtl g;
 };
 
+// a one-member launch: the member and launch descriptors travel as kernel
+// parameters of k_init_one instead of host-to-device copies
+struct InitOneArgs {
+    alignas(16) unsigned char mdev[sizeof(SolverBlock::dev)];
+    SolverBlock *blk;
+    struct EnsDesc *desc;
+    sw_solve_stats *stats;
+    int grid, nb0, cache_const, cache_state;
+};
+
 // members of one persistent launch and their block ranges
 struct EnsDesc {
     int n, grid;

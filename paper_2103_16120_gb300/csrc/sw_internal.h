@@ -13,6 +13,7 @@ struct sw_model_s;
 namespace sw {
 
 struct EnsDesc;
+struct InitOneArgs;
 
 template <class CT>
 struct OpArgs {
@@ -59,6 +60,8 @@ cudaError_t launch_fill(double *p, size_t n, double v, cudaStream_t s);
 cudaError_t set_barrier_debug(unsigned long long extra, unsigned long long limit_ns);
 // every member of a launch descriptor: initial GCR state, cleared barrier
 cudaError_t launch_init_members(const EnsDesc *Ddev, int n, cudaStream_t s);
+// one member: writes its descriptor, the launch descriptor and the initial state
+cudaError_t launch_init_one(const InitOneArgs &a, cudaStream_t s);
 // the member's e from an FP32 field (the network's direction)
 cudaError_t launch_store_e(int prec, const void *Mdev, const float *ef, int nx, int ny, int threads, cudaStream_t s);
 // the learned preconditioner applied to the residual r (FP64 or FP32) of

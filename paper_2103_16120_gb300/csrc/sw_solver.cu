@@ -1098,6 +1098,40 @@ cudaError_t launch_init_members(const EnsDesc *Ddev, int n, cudaStream_t s)
     return cudaGetLastError();
 }
 
+__global__ void k_init_one(const __grid_constant__ InitOneArgs a)
+{
+    static_assert(sizeof(SolverBlock::dev) % 4 == 0, "member descriptor copied as 32-bit words");
+    constexpr int W = (int)(sizeof(SolverBlock::dev) / 4);
+    const unsigned *src = reinterpret_cast<const unsigned *>(a.mdev);
+    unsigned *dst = reinterpret_cast<unsigned *>(a.blk->dev);
+    for (int k = threadIdx.x; k < W; k += blockDim.x) dst[k] = src[k];
+    if (threadIdx.x == 0) {
+        EnsDesc *D = a.desc;
+        D->n = 1;
+        D->grid = a.grid;
+        D->cache_const = a.cache_const;
+        D->cache_state = a.cache_state;
+        D->stats = a.stats;
+        D->cta_begin[0] = 0;
+        D->cta_begin[1] = a.nb0;
+        D->blk[0] = a.blk;
+        MemberCtl c = {};
+        c.phase = PH_TRUE;
+        c.init = 1;
+        c.nu = -1;
+        a.blk->ctl = c;
+        a.blk->g.count = 0;
+        a.blk->g.abort = 0;
+        a.blk->g.where = 0;
+    }
+}
+
+cudaError_t launch_init_one(const InitOneArgs &a, cudaStream_t s)
+{
+    k_init_one<<<1, 128, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
 
 #ifdef SW_PHASE_TRACE
 // configure the device timeline (traced builds only): buffer of 2*cap words
