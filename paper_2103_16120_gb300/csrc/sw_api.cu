@@ -319,10 +319,7 @@ extern "C" sw_status sw_elliptic_set_coeffs(sw_grid g, const double *A11, const 
     a.ax = g->ax; a.cx = g->cx; a.bx = g->bx; a.ay = g->ay; a.cy = g->cy; a.by = g->by; a.C64 = g->C; a.diag = g->diag;
     a.wax = g->wax; a.wcx = g->wcx; a.wbx = g->wbx; a.way = g->way; a.wcy = g->wcy; a.wby = g->wby; a.wC = g->wC;
     a.wdiag = g->wdiag; a.rowmax = g->rowmax;
-    // k_faces is latency-bound with one block per row: as many threads as the row
-    // has points, up to the block limit (the scans of k_factor need fewer)
-    const int fthreads = g->nx < MAX_THREADS ? ((g->nx + 31) / 32) * 32 : MAX_THREADS;
-    CK(launch_faces(a, fthreads, s));
+    CK(launch_faces(a, row_threads(g->nx), s));
     sw_status st = refactor(g, s);
     if (st) return st;
     g->has_coeffs = true;

@@ -53,11 +53,10 @@ def test_async_equals_sync(prec):
 
 
 def test_back_to_back_async_solves_of_one_grid():
-    """A warm-started sequence enqueued without synchronisation: each call
-    stages its descriptors in the grid's ring of pinned slots, so later calls
-    (more of them than the ring holds) cannot overwrite what an earlier,
-    not yet executed, copy reads.  Each step between the solves changes the
-    coefficients too."""
+    """A warm-started sequence enqueued without synchronisation: with one
+    member each call's descriptors are kernel parameters of its launch, so
+    later calls cannot overwrite what an earlier, not yet executed, launch
+    reads.  Each step between the solves changes the coefficients too."""
     nx, ny, n = 256, 128, 7
     Ps = [synth.sequence_problem(nx, ny, 9100, t) for t in range(n)]
     cos = [[torch.as_tensor(P[k], device="cuda") for k in sw.COEFF_KEYS] for P in Ps]
@@ -122,3 +121,43 @@ def test_autotuner_picks_a_width_and_caches_it():
     assert again.threads_per_row == best.threads_per_row and table2 is table
     sts = sw.sw_ensemble_solve(grids, best, Rs, phis)
     assert all(s.status == sw.SW_OK and s.true_rel_residual <= 1e-8 for s in sts)
+
+
+def test_one_member_graph_replays_with_new_right_hand_sides():
+    """One member: the descriptors are kernel parameters recorded in the graph.
+    Replays after new contents of R (the same buffer) give the direct solves'
+    results, and a direct call on the same grid between replays, into another
+    buffer, disturbs neither."""
+    nx, ny = 256, 128
+    Ps = [synth.sequence_problem(nx, ny, 9200, t) for t in range(3)]
+    g = sw.sw_grid_create(nx, ny)
+    sw.sw_elliptic_set_coeffs(g, *[torch.as_tensor(Ps[0][k], device="cuda") for k in sw.COEFF_KEYS])
+    o = sw.sw_solve_opts_default(prec=sw.SW_PREC_MIXED_FP16, tol=1e-8)
+    Rs = [torch.as_tensor(P["R"], device="cuda") for P in Ps]
+    ref = []
+    for Rt in Rs:
+        x = torch.zeros_like(Rt)
+        st = sw.sw_gcr_solve(g, o, Rt, x)
+        assert st.status == sw.SW_OK
+        ref.append((x, st.iterations))
+    R = Rs[0].clone()
+    phi = torch.zeros_like(R)
+    buf = sw.stats_buffer(1)
+    graph = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(graph, stream=s):
+            phi.zero_()
+            sw.sw_ensemble_solve_async([g], o, [R], [phi], buf)
+    torch.cuda.current_stream().wait_stream(s)
+    for t in (2, 0, 1):
+        R.copy_(Rs[t])
+        graph.replay()
+        other, obuf = torch.zeros_like(R), sw.stats_buffer(1)
+        sw.sw_ensemble_solve_async([g], o, [Rs[t]], [other], obuf)
+        torch.cuda.synchronize()
+        got = sw.stats_from_device(buf, 1)[0]
+        assert got.status == sw.SW_OK and got.iterations == ref[t][1]
+        assert torch.equal(phi, ref[t][0]) and torch.equal(other, ref[t][0])
+        assert sw.stats_from_device(obuf, 1)[0].iterations == ref[t][1]
