@@ -358,7 +358,7 @@ def run_gpu(args):
     except Exception:
         pass
     peak = peaks.get("hbm_gbs", 6800.0)
-    launches_per_step = 4   # k_faces, k_factor<float>, k_init_members, k_gcr
+    launches_per_step = 4   # k_faces, k_factor<float>, k_init_one, k_gcr
     if rank == 0:
         print(json.dumps({
             "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,

@@ -92,9 +92,9 @@ def store_q(q, fmt: str, band: int):
 
 
 def default_band(ny: int) -> int:
-    """Pole-band rows at each pole: 1/2/3 at 64/128/256 rows (Sec. 4.3), one
-    more per doubling of the rows."""
-    b = max(1, int(np.floor(np.log2(ny))) - 5)
+    """Pole-band rows at each pole: 1/2/3 at 64/128/256 rows (Sec. 4.3), a band
+    of fixed angular width in general, round(3 ny / 256) rows."""
+    b = max(1, (3 * ny + 128) // 256)
     return min(b, ny // 2)
 
 

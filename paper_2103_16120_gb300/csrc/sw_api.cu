@@ -370,10 +370,9 @@ static int pole_band(const sw_grid_s *g, const sw_solve_opts *o)
 {
     if (o->prec == SW_PREC_FP64) return 0;
     if (o->pole_band_rows >= 0) return std::min(o->pole_band_rows, g->ny / 2);
-    // 1 / 2 / 3 rows at ny = 64 / 128 / 256 (Sec. 4.3), one more per doubling
-    int l = 0;
-    while ((1 << (l + 1)) <= g->ny) ++l;
-    int b = l - 5;
+    // a band of fixed angular width: 1 / 2 / 3 rows at ny = 64 / 128 / 256
+    // (Sec. 4.3), round(3 ny / 256) rows in general
+    int b = (3 * g->ny + 128) / 256;
     if (b < 1) b = 1;
     return std::min(b, g->ny / 2);
 }
