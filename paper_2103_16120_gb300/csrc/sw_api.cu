@@ -588,6 +588,51 @@ static sw_status check_members(int n, const sw_grid *grids, const sw_solve_opts 
     return SW_OK;
 }
 
+// one member: its descriptor and the launch descriptor go to the device as
+// kernel parameters of k_init_one (no host staging, no copies; a graph capture
+// records them by value)
+static sw_status solve_one_async(sw_grid g, const sw_solve_opts *o, const double *R, double *phi,
+                                 sw_solve_stats *stats_dev, int max_nx, cudaStream_t s)
+{
+    sw_status st;
+    if (o->eta > 0.0 && o->eta != g->eta_explicit) {
+        g->eta_explicit = o->eta;
+        if ((st = refactor(g, s))) return st;
+    }
+    if ((st = ensure_ws(g, o->prec, o->k))) return st;
+    if (o->prec == SW_PREC_FP64 && (st = ensure_f64(g, s))) return st;
+    InitOneArgs a;
+    std::memset(&a, 0, sizeof(a));
+    if (o->prec == SW_PREC_FP64) {
+        MemberDev<PolFP64> M;
+        fill_member<PolFP64>(g, o, R, phi, M);
+        std::memcpy(a.mdev, &M, sizeof(M));
+    } else if (o->prec == SW_PREC_MIXED_FP16) {
+        MemberDev<PolF16> M;
+        fill_member<PolF16>(g, o, R, phi, M);
+        std::memcpy(a.mdev, &M, sizeof(M));
+    } else {
+        MemberDev<PolBF16> M;
+        fill_member<PolBF16>(g, o, R, phi, M);
+        std::memcpy(a.mdev, &M, sizeof(M));
+    }
+    if (o->res_history) CK(launch_fill(o->res_history, (size_t)o->max_iters + 1, NAN, s));
+    Plan P;
+    if ((st = plan_launch(1, &g, o, max_nx, P))) return st;
+    a.blk = g->blk;
+    a.desc = g->desc;
+    a.stats = stats_dev;
+    a.grid = P.grid;
+    a.nb0 = P.nb[0];
+    a.cache_const = P.cc;
+    a.cache_state = P.cs;
+    CK(launch_init_one(a, s));
+    CK(launch_gcr(o->prec, o->k, P.minb, g->desc, P.grid, max_nx, P.threads, P.smem, s));
+    return SW_OK;
+}
+
+static sw_status finish_members(int n, const sw_grid *grids, sw_solve_stats *stats, cudaStream_t s);
+
 static sw_status solve_members(int n, const sw_grid *grids, const sw_solve_opts *o, const double *const *R,
                                double *const *phi, sw_solve_stats *stats, cudaStream_t s)
 {
@@ -612,6 +657,11 @@ static sw_status solve_members(int n, const sw_grid *grids, const sw_solve_opts 
         if (n > 1 && (o->res_history || o->row_residual))
             return fail(SW_ERR_INVALID_ARG, "res_history / row_residual are for single solves");
         max_nx = std::max(max_nx, g->nx);
+    }
+    if (n == 1 && o->pc != SW_PC_LEARNED) {
+        // one member: descriptors as kernel parameters, stats read back below
+        if ((st = solve_one_async(grids[0], o, R[0], phi[0], nullptr, max_nx, s))) return st;
+        return finish_members(n, grids, stats, s);
     }
     static thread_local std::vector<unsigned char> staging;
     staging.resize((size_t)n * sizeof(SolverBlock::dev));
@@ -663,6 +713,13 @@ static sw_status solve_members(int n, const sw_grid *grids, const sw_solve_opts 
             CK(launch_gcr(o->prec, o->k, P.minb, lead->desc, grid, max_nx, threads, smem, s));
         }
     }
+    return finish_members(n, grids, stats, s);
+}
+
+// wait for a synchronous solve and fill the host stats from each member's
+// final state
+static sw_status finish_members(int n, const sw_grid *grids, sw_solve_stats *stats, cudaStream_t s)
+{
     for (int m = 0; m < n; ++m) {
         sw_grid g = grids[m];
         CK(cudaMemcpyAsync(g->h_ctl, &g->blk->ctl, sizeof(MemberCtl) + sizeof(GlobalCtl), cudaMemcpyDeviceToHost, s));
@@ -838,49 +895,6 @@ extern "C" sw_status sw_gcr_solve_noalloc(sw_grid g, const sw_solve_opts *o, con
 
 // ---------------------------------------------------------------------------
 // ensemble solve without host synchronisation
-// one member: its descriptor and the launch descriptor go to the device as
-// kernel parameters of k_init_one (no host staging, no copies; a graph capture
-// records them by value)
-static sw_status solve_one_async(sw_grid g, const sw_solve_opts *o, const double *R, double *phi,
-                                 sw_solve_stats *stats_dev, int max_nx, cudaStream_t s)
-{
-    sw_status st;
-    if (o->eta > 0.0 && o->eta != g->eta_explicit) {
-        g->eta_explicit = o->eta;
-        if ((st = refactor(g, s))) return st;
-    }
-    if ((st = ensure_ws(g, o->prec, o->k))) return st;
-    if (o->prec == SW_PREC_FP64 && (st = ensure_f64(g, s))) return st;
-    InitOneArgs a;
-    std::memset(&a, 0, sizeof(a));
-    if (o->prec == SW_PREC_FP64) {
-        MemberDev<PolFP64> M;
-        fill_member<PolFP64>(g, o, R, phi, M);
-        std::memcpy(a.mdev, &M, sizeof(M));
-    } else if (o->prec == SW_PREC_MIXED_FP16) {
-        MemberDev<PolF16> M;
-        fill_member<PolF16>(g, o, R, phi, M);
-        std::memcpy(a.mdev, &M, sizeof(M));
-    } else {
-        MemberDev<PolBF16> M;
-        fill_member<PolBF16>(g, o, R, phi, M);
-        std::memcpy(a.mdev, &M, sizeof(M));
-    }
-    if (o->res_history) CK(launch_fill(o->res_history, (size_t)o->max_iters + 1, NAN, s));
-    Plan P;
-    if ((st = plan_launch(1, &g, o, max_nx, P))) return st;
-    a.blk = g->blk;
-    a.desc = g->desc;
-    a.stats = stats_dev;
-    a.grid = P.grid;
-    a.nb0 = P.nb[0];
-    a.cache_const = P.cc;
-    a.cache_state = P.cs;
-    CK(launch_init_one(a, s));
-    CK(launch_gcr(o->prec, o->k, P.minb, g->desc, P.grid, max_nx, P.threads, P.smem, s));
-    return SW_OK;
-}
-
 // ---------------------------------------------------------------------------
 extern "C" sw_status sw_ensemble_solve_async(int n, const sw_grid *grids, const sw_solve_opts *o,
                                              const double *const *R, double *const *phi,

@@ -188,3 +188,28 @@ def test_step_argument_errors():
         sw.sw_swe_step(m, o, 0)
     with pytest.raises(sw.SwError):
         sw.sw_swe_step(m, sw.sw_solve_opts_default(pc=sw.SW_PC_LEARNED), 1)
+
+
+def test_full_size_steps_keep_mass_and_stay_bounded():
+    """2048 x 1024 (the largest benchmark grid), three mixed steps at the
+    paper's scaling of dt (50 s): mass moves only within the solves' residual
+    bound, the state stays finite and positive, and the advective Courant
+    number stays below 1 on every row, pole rows included."""
+    nx, ny = 2048, 1024
+    dt = synth.paper_dt(ny)
+    s = synth.perturbed_state(nx, ny, 77, dt=dt, orography=500.0)
+    g = sw.sw_grid_create(nx, ny)
+    m = sw.sw_swe_create(g, dt)
+    sw.sw_swe_set_state(m, dev(s.phi), dev(s.qx), dev(s.qy), dev(s.h0), dev(s.alpha), dev(s.qbar_x),
+                        dev(s.qbar_y))
+    stats = sw.sw_swe_step(m, sw.sw_solve_opts_default(prec=sw.SW_PREC_MIXED_FP16, tol=1e-8, max_iters=2000), 3)
+    assert all(x.converged == 1 and x.true_rel_residual <= 1e-8 for x in stats)
+    p, qx, qy = state(m)
+    assert np.all(np.isfinite(p)) and np.min(p) > 0 and np.all(np.isfinite(qx)) and np.all(np.isfinite(qy))
+    lam, phi, dlam, dphi = synth.grid_coords(nx, ny)
+    cw = np.cos(phi)[:, None]
+    bound = sum(math.sqrt(nx * ny) * x.true_rel_residual * x.R_norm for x in stats[1::2]) * (0.5 * dt) / A ** 2
+    m0 = float(np.sum(cw * s.phi))
+    assert abs(float(np.sum(cw * p)) - m0) <= 1.01 * bound + 1e-13 * m0
+    courant = np.max(np.abs(qx / p) / cw) * dt / (A * dlam)
+    assert courant < 1.0
