@@ -138,8 +138,54 @@ __device__ void phase_true(const MemberDev<Pol> &M, const RowView<Pol> &v, typen
     auto wrap = [&](int i) { return i >= nx ? i - nx : i; };
     const bool has_n = j < ny - 1, has_s = j > 0;
     double rr = 0.0, RR = 0.0;
+    // rows away from the poles (no shifted neighbour row): 4 consecutive points
+    // per thread, each zonal face flux formed once for its two points (the same
+    // expressions as below, so L(Phi) is unchanged)
+    const bool v4 = sh[0] == 0 && sh[2] == 0 && stencil4_ok(c, nx) && al16p(ph) && al16p(M.R + row);
+    if (v4) {
+        for (int i0 = 4 * threadIdx.x; i0 < nx; i0 += 4 * blockDim.x) {
+            double xc[6], xn[6], xs[6];
+            ldw6(pX, i0, nx, xc);
+            ldw6(pN, i0, nx, xn);
+            ldw6(pS, i0, nx, xs);
+            const int iw = i0 == 0 ? nx - 1 : i0 - 1;
+            double ax[5], cx[5], bx[5], q[4];
+            ax[0] = c.ax[iw]; cx[0] = c.cx[iw]; bx[0] = c.bx[iw];
+            ldv4(c.ax + i0, q); for (int k = 0; k < 4; ++k) ax[k + 1] = q[k];
+            ldv4(c.cx + i0, q); for (int k = 0; k < 4; ++k) cx[k + 1] = q[k];
+            ldv4(c.bx + i0, q); for (int k = 0; k < 4; ++k) bx[k + 1] = q[k];
+            double cc[4], Rv[4];
+            ldv4(c.C + i0, cc);
+            ldv4(M.R + row + i0, Rv);
+            double ay[4] = {}, cy[4] = {}, by[4] = {}, ays[4] = {}, cys[4] = {}, bys[4] = {};
+            if (has_n) { ldv4(c.ay + i0, ay); ldv4(c.cy + i0, cy); ldv4(c.by + i0, by); }
+            if (has_s) { ldv4(c.ays + i0, ays); ldv4(c.cys + i0, cys); ldv4(c.bys + i0, bys); }
+            // face m: east face of window point m (window k = longitude i0 - 1 + k)
+            double F[5];
+#pragma unroll
+            for (int m = 0; m < 5; ++m)
+                F[m] = cx[m] * (xn[m] + xn[m + 1] - xs[m] - xs[m + 1]) + bx[m] * (xc[m] + xc[m + 1]) +
+                       ax[m] * (xc[m + 1] - xc[m]);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int k = u + 1, i = i0 + u;
+                double lphi = F[u + 1] - F[u];
+                if (has_n) lphi += ay[u] * (xn[k] - xc[k]) + cy[u] * (xc[k + 1] + xn[k + 1] - xc[k - 1] - xn[k - 1]) +
+                                   by[u] * (xc[k] + xn[k]);
+                if (has_s) lphi -= ays[u] * (xc[k] - xs[k]) + cys[u] * (xs[k + 1] + xc[k + 1] - xs[k - 1] - xc[k - 1]) +
+                                   bys[u] * (xs[k] + xc[k]);
+                lphi -= cc[u] * xc[k];
+                const double rv = lphi - Rv[u];
+                const typename Pol::res rs = (typename Pol::res)rv;
+                v.r[i] = rs;
+                rr += rv * rv;
+                RR += Rv[u] * Rv[u];
+                sb[pidx(i)] = stage0_input(M, v, eta, (comp)rs, i);
+            }
+        }
+    }
     constexpr int U = 2;
-    for (int i0 = threadIdx.x; i0 < nx; i0 += U * blockDim.x) {
+    for (int i0 = v4 ? nx : (int)threadIdx.x; i0 < nx; i0 += U * blockDim.x) {
         double cx[U], cxw[U], bx[U], bxw[U], ax[U], axw[U], ay[U], cy[U], by[U], ays[U], cys[U], bys[U], cc[U], Rv[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
