@@ -56,7 +56,7 @@ METRIC = "elliptic solves/s at 1e-8 rel. residual: mixed+learned vs FP64 GCR, sa
 NX, NY, NSEQ, SEED, TOL, K_GCR = 512, 256, 200, 1000, 1e-8, 4
 WORKLOAD = "sequence of 200 solves, 512x256 lon/lat grid, evolving coefficients, warm start"
 # DRAM bytes of one mixed-precision solve launch of this workload, measured with ncu
-TRAFFIC_512 = 15355136 + 6912
+TRAFFIC_512 = 15364864 + 7424
 KEYS = ("A11", "A12", "A21", "A22", "B1", "B2", "C")
 
 
