@@ -341,8 +341,8 @@ typedef struct {
     double omega;     /* rotation rate Omega (1/s) */
 } sw_swe_params;
 
-/* Create a stepper on grid g (which must outlive it); allocates about 35
- * fields of nx*ny doubles on the grid's device.  The grid's coefficients are
+/* Create a stepper on grid g (which must outlive it); allocates 38 fields of
+ * nx*ny doubles on the grid's device.  The grid's coefficients are
  * replaced at every step. */
 sw_status sw_swe_create(sw_grid g, const sw_swe_params *p, sw_swe *out);
 sw_status sw_swe_destroy(sw_swe m);

@@ -307,7 +307,7 @@ struct sw_swe_s {
     size_t N;
     sw_swe_params p;
     double radius;
-    double *mem = nullptr;       // F_COUNT fields, then the three row tables
+    double *mem = nullptr;       // F_COUNT fields, then the NROWTAB row tables
     double *f[F_COUNT];
     double *rows = nullptr;
     int cur = 0;                 // state buffer holding level n
