@@ -482,7 +482,7 @@ def run_learned(args):
         "metric": METRIC, "value": head["solves_per_s"], "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": head["ms_per_solve"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16 network (f32 accumulate), f32/f16 solver", "data": "synthetic",
-        "config": {"workload": "learned preconditioner at 256x128 (config 3)", "samples": n,
+        "config": {"workload": "learned preconditioner at 256x128, evaluated at 256x128 and 1024x512", "samples": n,
                    "epochs": args.epochs, "batch": B, "network": "3-level U-Net 32/64/64, 158369 parameters"},
         "solves": out,
         "training": {"ms_per_step": ms_step, "samples_per_s": B / (ms_step * 1e-3), "tflops": tflops,
@@ -572,7 +572,7 @@ def run_ensemble(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_ensemble"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 (f16 storage, f64 reductions)",
         "data": "synthetic",
-        "config": {"workload": "ensemble of 64 members in one persistent launch (config 2)",
+        "config": {"workload": "ensemble of 64 members (32 at 128x64, 24 at 256x128, 8 at 512x256) in one persistent launch",
                    "members": "32 x 128x64, 24 x 256x128, 8 x 512x256", "tol": TOL, "precision": "mixed-fp16"},
         "launch_per_member": res["launch_per_member"], "one_launch": res["one_launch"],
         "graph_replay": res["graph_replay"],
@@ -631,7 +631,7 @@ def run_large(args):
         "metric": METRIC, "value": mixed["solves_per_s"], "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": mixed["ms_per_solve"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32 (f16 storage, f64 reductions)", "data": "synthetic",
-        "config": {"workload": "2048x1024 solve sequence, warm start (config 4)", "tol": TOL, "k": K_GCR},
+        "config": {"workload": "2048x1024 solve sequence, warm start", "tol": TOL, "k": K_GCR},
         "fp64_gcr": {k: v for k, v in res["fp64"].items() if k != "phi"},
         "mixed": {k: v for k, v in mixed.items() if k != "phi"},
         "speedup_vs_fp64": mixed["solves_per_s"] / res["fp64"]["solves_per_s"],

@@ -177,14 +177,14 @@ def sequence_problem(nx: int, ny: int, seed: int, step: int, dt: float = 600.0) 
     return problem(nx, ny, seed, dt=dt, theta=step * SEQ_DTHETA)
 
 
-def ensemble_members(spec=((32, 128, 64), (24, 256, 128), (8, 512, 256)), config: int = 2):
+def ensemble_members(spec=((32, 128, 64), (24, 256, 128), (8, 512, 256)), seed_block: int = 2):
     """(nx, ny, seed) for each member of a batched ensemble; seeds are
-    1000*config + member index."""
+    1000*seed_block + member index."""
     out = []
     k = 0
     for count, nx, ny in spec:
         for _ in range(count):
-            out.append((nx, ny, 1000 * config + k))
+            out.append((nx, ny, 1000 * seed_block + k))
             k += 1
     return out
 

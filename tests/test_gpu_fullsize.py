@@ -2,9 +2,9 @@
 
 The oracle recomputes, in FP64 and with its own operator, the residual
 ||L(Phi) - R|| / ||R|| of the GPU's solutions:
-* the 2048 x 1024 problem (config 4), mixed FP16;
-* all 64 members of the ensemble (config 2), solved in one launch;
-* the first steps of the 512 x 256 warm-started sequence (config 1), whose
+* the 2048 x 1024 problem, mixed FP16;
+* all 64 members of the 128x64 / 256x128 / 512x256 ensemble, solved in one launch;
+* the first steps of the 512 x 256 warm-started sequence, whose
   solution is also compared with the oracle's own GCR solution;
 * FP64 iterates on 1024 x 512 and 2048 x 1024, where every block owns several
   rows, against the oracle's iterates (1e-12);
