@@ -19,7 +19,7 @@ before timing; successive steps read different sets, so the inputs of the
 timed region are larger than L2.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                  [--workload seq512|learned256|ensemble64|large2048|swe512]
+                  [--workload seq512|learned256|ensemble64|large2048|swe512|oracle]
 
 The default workload is the one above.  The others measure the remaining
 configurations on one GPU, one JSON line each:
@@ -34,6 +34,8 @@ configurations on one GPU, one JSON line each:
   swe512      the semi-implicit shallow-water model around the solver
               (Eqs. 1-10) at 512 x 256, dt = 200 s: model steps/s, two
               solves per step, mixed against FP64
+  oracle      the CPU FP64 oracle on the host alone: seconds per solve of
+              the workloads above, one thread and all host threads
 """
 from __future__ import annotations
 
@@ -774,6 +776,42 @@ def run_swe(args):
     }), flush=True)
 
 
+def run_oracle_timings(args):
+    """CPU oracle timings of the benchmark's workloads, one host thread and all
+    of them: the 128x64 single solve (20 solves, tol 1e-10), the first 10
+    solves of the 512x256 sequence, 2 solves of the 2048x1024 sequence (warm
+    start, tol 1e-8) and the 64 ensemble members one after another.  A
+    reported baseline, not a target; no GPU is used."""
+    import oracle as O
+    import oracle.oracle as orc
+    orc.build()
+    cores = cpu_cores()
+    cases = [
+        ("128x64 single solve, tol 1e-10", [synth.problem(128, 64, 0)] * 20, False, 1e-10),
+        ("512x256 sequence, first 10 solves", [synth.sequence_problem(NX, NY, SEED, t) for t in range(10)], True, TOL),
+        ("2048x1024 sequence, 2 solves", [synth.sequence_problem(2048, 1024, 4000, t) for t in range(2)], True, TOL),
+        ("ensemble members one after another",
+         [synth.problem(nx, ny, seed) for nx, ny, seed in synth.ensemble_members()], False, TOL),
+    ]
+    rows = {}
+    for label, probs, warm, tol in cases:
+        rows[label] = {}
+        for nth in (1, cores):
+            orc.set_threads(nth)
+            phi, its = None, []
+            t0 = time.perf_counter()
+            for P in probs:
+                phi, st = O.Problem(P).gcr(P["R"], O.Opts(k=K_GCR, tol=tol, max_iters=5000),
+                                           phi0=phi if warm else None)
+                its.append(st["iterations"])
+            dt = time.perf_counter() - t0
+            rows[label][f"threads_{nth}"] = {"s_per_solve": dt / len(probs), "solves": len(probs),
+                                             "mean_iterations": float(np.mean(its))}
+    orc.set_threads(cores)
+    print(json.dumps({"impl": "oracle", "metric": "CPU FP64 oracle seconds per solve", "unit": "s/solve",
+                      "higher_is_better": False, "cores": cores, "data": "synthetic", "timings": rows}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -781,7 +819,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gcr", choices=["gcr", "reference"])
     ap.add_argument("--workload", default="seq512",
-                    choices=["seq512", "learned256", "ensemble64", "large2048", "swe512"])
+                    choices=["seq512", "learned256", "ensemble64", "large2048", "swe512", "oracle"])
     ap.add_argument("--samples", type=int, default=20000, help="learned256: training triples")
     ap.add_argument("--epochs", type=int, default=4, help="learned256: training epochs")
     args = ap.parse_args()
@@ -797,6 +835,8 @@ def main():
         run_large(args)
     elif args.workload == "swe512":
         run_swe(args)
+    elif args.workload == "oracle":
+        run_oracle_timings(args)
     else:
         run_gpu(args)
 

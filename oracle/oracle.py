@@ -67,6 +67,8 @@ def _get():
         _lib.swo_gcr.restype = C.c_int
         _lib.swo_round_bits.argtypes = [C.c_double, C.c_int]
         _lib.swo_round_bits.restype = C.c_double
+        _lib.swo_set_threads.argtypes = [C.c_int]
+        _lib.swo_set_threads.restype = None
     return _lib
 
 
@@ -172,6 +174,11 @@ def cyclic_solve(sub, diag, sup, rhs):
     x = np.zeros(n)
     _get().swo_cyclic_solve(n, *[_ptr(a) for a in arrs], _ptr(x))
     return x
+
+
+def set_threads(n: int) -> None:
+    """Host threads of the oracle's row loops (results do not depend on it)."""
+    _get().swo_set_threads(int(n))
 
 
 def round_bits(x: float, p: int) -> float:

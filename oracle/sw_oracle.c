@@ -461,3 +461,17 @@ double swo_round_bits(double x, int p)
     double r = nearbyint(s);                  /* default mode: nearest, ties to even */
     return ldexp(r, ex - p - 1);
 }
+
+/* Host threads of the OpenMP row loops (timing only: the row loops and their
+ * fixed-order per-row partial sums give the same results for any count). */
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+void swo_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}

@@ -464,3 +464,17 @@ def test_round_bits_emulates_ieee_formats():
     ok &= np.abs(x) > 6.2e-5
     assert all(O.round_bits(a, p) == b for a, b, m in zip(x, f16, ok) if m)
     assert abs(2.0 ** -p - GOLDEN["half_machine_epsilon"]["value"]) < 1e-6
+
+
+def test_oracle_results_do_not_depend_on_the_thread_count():
+    """The row loops run in parallel with fixed-order per-row partial sums, so
+    one thread and all host threads give the same bits."""
+    import oracle.oracle as orc
+    P = synth.problem(128, 64, 5)
+    outs = []
+    for n in (1, 4):
+        orc.set_threads(n)
+        phi, st = O.Problem(P).gcr(P["R"], O.Opts(tol=1e-10, max_iters=500))
+        outs.append((phi, st["iterations"]))
+    orc.set_threads(os.cpu_count() or 1)
+    assert outs[0][1] == outs[1][1] and np.array_equal(outs[0][0], outs[1][0])
