@@ -17,7 +17,9 @@ Each test checks the oracle against something other than its own formulas:
   is the trapezoidal Eq. 1 with that flux;
 * donor-cell transport at Courant number 1 under a solid-body zonal rotation
   is an exact shift by one cell; in a meridional flow a one-cell spike moves
-  only into the downstream cell, by the donor-cell flux.
+  only into the downstream cell, by the donor-cell flux;
+* white noise on fluid at rest stays bounded at the paper's time step, and fluid
+  at rest over a flat bottom does not change in any bit.
 
 With these, a dropped term, a wrong sign or factor of the 2x2 inversion, the
 coefficients, the right-hand side or the transport fails at least one pin (each
@@ -265,3 +267,16 @@ def test_noise_does_not_grow_at_the_papers_time_step():
         assert info.stats["converged"] == 1
     assert np.max(np.abs(p - H)) <= 1.5 * np.max(np.abs(noise))
     assert np.max(np.abs(qx / p)) < 1.0 and np.max(np.abs(qy / p)) < 1.0
+
+
+def test_rest_state_is_exactly_steady():
+    """Fluid at rest over a flat bottom: every flux vanishes, C Phi^n cancels
+    L(Phi^n) exactly, the right-hand side of each solve is zero and the solves
+    return zero increments, so the state does not change in any bit."""
+    nx, ny, H = 32, 16, 8000.0
+    st = Stepper(nx, ny, 800.0)
+    p0 = np.full((ny, nx), H)
+    z = np.zeros((ny, nx))
+    p, qx, qy, infos = st.run(p0, z, z, 3)
+    assert all(np.all(i.rhs == 0.0) and i.stats["iterations"] == 0 for i in infos)
+    assert np.array_equal(p, p0) and not np.any(qx) and not np.any(qy)
