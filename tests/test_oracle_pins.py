@@ -263,6 +263,78 @@ def test_split_PZ_closed_form_and_PM_remainder():
 
 
 # --------------------------------------------------------------------------
+# eta, the pseudo time step of Eq. 13 (Sec. 2.3): 1 / max |diag(P^M)|
+# --------------------------------------------------------------------------
+def test_eta_auto_closed_form_meridional_diffusion():
+    """A22 = kappa alone: P^M is the meridional second difference with zero flux
+    through the pole faces, so diag(P^M) is -2 kappa/dphi^2 on interior rows and
+    -kappa/dphi^2 on the two pole rows; eta = dphi^2 / (2 kappa)."""
+    for nx, ny, kappa in [(16, 8, 3.5e6), (48, 20, 0.7), (8, 3, 1e12)]:
+        _, _, _, dphi = grid_coords(nx, ny)
+        eta = O.Problem(_const_coeffs(nx, ny, A22=kappa)).eta_auto()
+        assert abs(eta - dphi ** 2 / (2 * kappa)) <= 1e-14 * eta
+    # two rows: both are pole rows, each with one meridional face
+    _, _, _, dphi = grid_coords(8, 2)
+    eta = O.Problem(_const_coeffs(8, 2, A22=2.0)).eta_auto()
+    assert abs(eta - dphi ** 2 / 2.0) <= 1e-14 * eta
+
+
+def test_eta_auto_ignores_the_implicit_part_and_the_cross_terms():
+    """The zonal A11 part and C form T = I - eta (P^Z - P^H) and are not in P^M;
+    the cross terms A12, A21 never touch the centre point (even across a pole,
+    where the ghost is shifted by nx/2).  Adding any of them leaves eta at the
+    closed form of A22 alone.  Fails for diag(L) in place of diag(P^M), a
+    dropped +C or a dropped A11 removal."""
+    nx, ny, kappa = 24, 12, 4.0e5
+    _, _, _, dphi = grid_coords(nx, ny)
+    rng = np.random.default_rng(31)
+    c = _const_coeffs(nx, ny, A22=kappa)
+    c["A11"] = 1e7 * (1 + rng.random((ny, nx)))
+    c["C"] = 1e9 * (1 + rng.random((ny, nx)))
+    c["A12"] = 3e5 * rng.standard_normal((ny, nx))
+    c["A21"] = -c["A12"] + 1e5 * rng.standard_normal((ny, nx))
+    eta = O.Problem(c).eta_auto()
+    assert abs(eta - dphi ** 2 / (2 * kappa)) <= 1e-13 * eta
+
+
+def test_eta_auto_closed_form_advective_terms():
+    """B2 = b (constant) with A22 = kappa: the centred meridional mean puts
+    +b/(2 dphi) on the first row (north face only) and -b/(2 dphi) on the last
+    (south face only), and cancels inside.  With b > 2 kappa/dphi the pole rows
+    set eta = 1 / (kappa/dphi^2 + b/(2 dphi)).  B1 = beta sin(lambda) alone puts
+    (B1[i+1] - B1[i-1]) / (4 dlam) = beta cos(lambda_i) sin(dlam) / (2 dlam) on
+    the diagonal, largest at lambda = 0: eta = 2 dlam / (beta sin dlam).  A
+    dropped or mis-signed B term fails these."""
+    nx, ny, kappa = 32, 16, 1.0
+    lam, _, dlam, dphi = grid_coords(nx, ny)
+    b = 5 * kappa / dphi
+    eta = O.Problem(_const_coeffs(nx, ny, A22=kappa, B2=b)).eta_auto()
+    want = 1.0 / (kappa / dphi ** 2 + b / (2 * dphi))
+    assert abs(eta - want) <= 1e-14 * want
+    # B2 alone: only the pole rows see it
+    eta = O.Problem(_const_coeffs(nx, ny, B2=b)).eta_auto()
+    assert abs(eta - 2 * dphi / b) <= 1e-14 * eta
+    beta = 7.0
+    eta = O.Problem(_const_coeffs(nx, ny, B1=beta * np.sin(lam)[None, :])).eta_auto()
+    want = 2 * dlam / (beta * math.sin(dlam))
+    assert abs(eta - want) <= 1e-13 * want
+
+
+def test_eta_auto_equals_assembled_PM_diagonal():
+    """Brute force on the synthetic problem: assemble P^M column by column
+    (P^M = L - P^Z + C, itself pinned above) and take 1/max|diag|."""
+    nx, ny = 16, 8
+    P = synth.problem(nx, ny, 17)
+    prob = O.Problem(P)
+    n = nx * ny
+    dm = np.empty(n)
+    for c in range(n):
+        e = np.zeros(n); e[c] = 1.0
+        dm[c] = prob.apply_PM(e.reshape(ny, nx)).ravel()[c]
+    assert abs(prob.eta_auto() - 1.0 / np.max(np.abs(dm))) <= 1e-13 / np.max(np.abs(dm))
+
+
+# --------------------------------------------------------------------------
 # cyclic tridiagonal solve and the preconditioner (Eq. 13)
 # --------------------------------------------------------------------------
 @pytest.mark.parametrize("n", [3, 4, 7, 64, 129])
