@@ -1,28 +1,33 @@
 """Benchmark: elliptic solves/s to a 1e-8 relative residual on one GB300.
 
-Workload (one "step" = one elliptic solve of the sequence): a sequence of 200
-solves on a 512 x 256 lon/lat grid whose coefficients evolve smoothly between
-solves (seeded synthetic shallow-water states, dt = 600 s), each warm-started
-from the previous solution.  Each step runs the whole hot path through the C
-ABI: sw_elliptic_set_coeffs (face coefficients, automatic eta, factorised
-zonal operators) and the solve (GCR(4) with the semi-implicit Richardson
+Default workload (one "step" = one elliptic solve of the sequence): a
+sequence of 100 solves on a 2048 x 1024 lon/lat grid (about 2.1 M unknowns)
+whose coefficients evolve smoothly between solves (seeded synthetic
+shallow-water states, dt = 600 s), each warm-started from the previous
+solution.  Each step runs the whole hot path through the C ABI:
+sw_elliptic_set_coeffs (face coefficients, automatic eta, factorised zonal
+operators) and the solve (GCR(4) with the semi-implicit Richardson
 preconditioner, true residual <= 1e-8 ||R||), enqueued with
-sw_ensemble_solve_async so that the host prepares the next step while the GPU
-solves; every step's stats go to device memory and are checked after the
-timed region.  The headline `value` is the
-mixed-precision solver (FP16 preconditioner storage with per-row scaling, FP32
-operator and recursive residual, FP64 inner products, solution and true
-residual); the plain FP64 GPU GCR is timed the same way and reported beside it.
+sw_ensemble_solve_async so that the host prepares the next step while the
+GPU solves; every step's stats go to device memory and are checked after the
+timed region.  The headline `value` is the mixed-precision solver (FP16
+preconditioner storage with per-row scaling, FP32 operator and recursive
+residual, FP64 inner products, solution and true residual); the plain FP64
+GPU GCR is timed the same way and reported beside it, and so is the mixed
+solver with the learned preconditioner (a network trained in the same run on
+256 x 128 solver-generated triples and applied at 2048 x 1024 without
+retraining).  The solution error of each arm is measured against the FP64
+CPU oracle on the sequence's first problem.
 
-All 200 coefficient sets and right-hand sides (1.7 GB) are resident in HBM
-before timing; successive steps read different sets, so the inputs of the
-timed region are larger than L2.
+The coefficient sets and right-hand sides of the timed steps (134 MB each)
+are resident in HBM before timing; every set is larger than L2.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                  [--workload seq512|learned256|ensemble64|large2048|swe512|oracle]
+                  [--workload seq2048|seq512|learned256|ensemble64|swe512|oracle]
 
-The default workload is the one above.  The others measure the remaining
-configurations on one GPU, one JSON line each:
+The other workloads measure the remaining configurations on one GPU, one
+JSON line each:
+  seq512      the same sequence measurement on a 512 x 256 grid (200 solves)
   learned256  the learned preconditioner at 256 x 128: GPU training on solver
               generated triples (tensor-core throughput against the BF16
               peak), then flexible-GCR solves against option 3 at 256 x 128
@@ -30,7 +35,6 @@ configurations on one GPU, one JSON line each:
   ensemble64  64 independent members (32 at 128x64, 24 at 256x128, 8 at
               512x256) in one persistent launch, against the same members
               solved one launch each
-  large2048   solves of a 2048 x 1024 sequence, mixed against FP64
   swe512      the semi-implicit shallow-water model around the solver
               (Eqs. 1-10) at 512 x 256, dt = 200 s: model steps/s, two
               solves per step, mixed against FP64
@@ -56,10 +60,20 @@ import synth  # noqa: E402
 
 METRIC = "elliptic solves/s at 1e-8 rel. residual: mixed+learned vs FP64 GCR, same GB300"
 NX, NY, NSEQ, SEED, TOL, K_GCR = 512, 256, 200, 1000, 1e-8, 4
-WORKLOAD = "sequence of 200 solves, 512x256 lon/lat grid, evolving coefficients, warm start"
-# DRAM bytes of one mixed-precision solve launch of this workload, measured with ncu
-TRAFFIC_512 = 15364864 + 7424
 KEYS = ("A11", "A12", "A21", "A22", "B1", "B2", "C")
+
+# the solve sequences: grid, length, seed of the seeded synthetic states
+SEQS = {
+    "seq2048": {"nx": 2048, "ny": 1024, "nseq": 100, "seed": 4000,
+                "label": "sequence of 100 solves, 2048x1024 lon/lat grid, evolving coefficients, warm start"},
+    "seq512": {"nx": 512, "ny": 256, "nseq": 200, "seed": 1000,
+               "label": "sequence of 200 solves, 512x256 lon/lat grid, evolving coefficients, warm start"},
+}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum, ncu) of the
+# mixed-precision solver kernel per launch (seq512) or per GCR iteration
+# (seq2048, scaled by the launch's iterations); None until captured for the
+# current kernel
+TRAFFIC = {"seq512": None, "seq2048_per_iteration": None}
 
 
 def dist_env():
@@ -80,8 +94,9 @@ def max_over_ranks(ms: float, world: int, device) -> float:
     return float(t.item())
 
 
-def make_sequence(n: int):
-    return [synth.sequence_problem(NX, NY, SEED, t) for t in range(n)]
+def make_sequence(n: int, wl: str = "seq512"):
+    q = SEQS[wl]
+    return [synth.sequence_problem(q["nx"], q["ny"], q["seed"], t) for t in range(min(n, q["nseq"]))]
 
 
 # ---------------------------------------------------------------------------
@@ -89,19 +104,33 @@ def make_sequence(n: int):
 # ---------------------------------------------------------------------------
 def oracle_solves(seq, budget_s: float, max_solves: int):
     import oracle as O
-    phi = np.zeros((NY, NX))
+    ny, nx = seq[0]["C"].shape
+    phi = np.zeros((ny, nx))
     t0 = time.perf_counter()
     n = 0
     its = []
     while n < max_solves:
         P = seq[n % len(seq)]
-        phi, st = O.Problem(P).gcr(P["R"], O.Opts(k=K_GCR, tol=TOL, max_iters=2000), phi0=phi)
+        phi, st = O.Problem(P).gcr(P["R"], O.Opts(k=K_GCR, tol=TOL, max_iters=4000), phi0=phi)
         its.append(st["iterations"])
         n += 1
         if time.perf_counter() - t0 > budget_s:
             break
     dt = time.perf_counter() - t0
     return n, dt, its
+
+
+def oracle_reference_solve(P, tol: float = 1e-10):
+    """The FP64 oracle's solve of one problem from a zero first guess, to tol.
+    Returns the solution, the wall time, the iterations it took and the
+    iteration at which its residual first met the benchmark tolerance."""
+    import oracle as O
+    t0 = time.perf_counter()
+    phi, st, hist, _ = O.Problem(P).gcr(P["R"], O.Opts(k=K_GCR, tol=tol, max_iters=6000), want_history=True)
+    dt = time.perf_counter() - t0
+    at = np.nonzero(hist <= TOL)[0]
+    its_tol = int(at[0]) if at.size else int(st["iterations"])
+    return phi, dt, int(st["iterations"]), its_tol
 
 
 def cpu_cores():
@@ -112,27 +141,64 @@ def cpu_cores():
 
 
 def run_reference(args):
+    """The reference arm: the FP64 CPU oracle on the host cores, on the same
+    workload, metric and unit as the GPU arm.  seq512: each step is one
+    warm-started oracle solve of the sequence.  seq2048: one oracle solve takes
+    tens of seconds, so each step is a bounded sample of 8 GCR iterations of
+    the sequence's next problem (warm-started from the previous step), and the
+    time per iteration is scaled to solves/s by the iterations the oracle
+    needs for the sequence's first problem (measured once, untimed)."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
+    import oracle as O
     import oracle.oracle as orc
     orc.build()
     cores = cpu_cores()
     os.environ.setdefault("OMP_NUM_THREADS", str(cores))
-    seq = make_sequence(min(NSEQ, args.steps + args.warmup + 1))
-    oracle_solves(seq, 1e9, args.warmup)   # warm-up solves (untimed)
-    n, dt, its = oracle_solves(seq, 1e9, args.steps)
-    v = n / dt
-    sample = f"{n} FP64 oracle solves of the 512x256 sequence (warm start), {cores} host threads"
+    wl = args.workload if args.workload in SEQS else "seq2048"
+    q = SEQS[wl]
+    seq = make_sequence(args.steps + args.warmup + 1, wl)
+    extra = {}
+    if wl == "seq512":
+        oracle_solves(seq, 1e9, args.warmup)   # warm-up solves (untimed)
+        n, dt, its = oracle_solves(seq, 1e9, args.steps)
+        v = n / dt
+        ms = 1e3 * dt / n
+        sample = f"{n} FP64 oracle solves of the 512x256 sequence (warm start), {cores} host threads"
+        extra["mean_iterations"] = float(np.mean(its))
+    else:
+        _, _, its_full, its_tol = oracle_reference_solve(seq[0], tol=TOL)
+        per = 8
+        phi = np.zeros((q["ny"], q["nx"]))
+
+        def sample_step(t):
+            nonlocal phi
+            P = seq[t % len(seq)]
+            phi, st = O.Problem(P).gcr(P["R"], O.Opts(k=K_GCR, tol=0.0, max_iters=per), phi0=phi)
+
+        for t in range(args.warmup):
+            sample_step(t)
+        t0 = time.perf_counter()
+        for t in range(args.warmup, args.warmup + args.steps):
+            sample_step(t)
+        dt = time.perf_counter() - t0
+        s_per_it = dt / (args.steps * per)
+        v = 1.0 / (s_per_it * its_tol)
+        ms = 1e3 / v
+        sample = (f"{args.steps} steps of {per} FP64 oracle GCR iterations each on the 2048x1024 sequence "
+                  f"(warm start), scaled by the {its_tol} iterations the oracle takes to 1e-8 on the first "
+                  f"problem; {cores} host threads")
+        extra["oracle_iterations_per_solve"] = its_tol
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / n, "higher_is_better": True,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "nx": NX, "ny": NY, "tol": TOL, "k": K_GCR,
+        "config": {"workload": q["label"], "nx": q["nx"], "ny": q["ny"], "tol": TOL, "k": K_GCR,
                    "preconditioner": "semi-implicit Richardson, 2 iterations", "oracle": "CPU FP64"},
         "cpu_baseline": {"value": v, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-        "mean_iterations": float(np.mean(its)),
+        **extra,
     }), flush=True)
 
 
@@ -211,11 +277,59 @@ def algorithmic_bytes_per_point(prec_mixed: bool, its: float, stages: int = 2, k
     return per_it * its + setup + true_res
 
 
+def learned_arm(sw, torch, dev, P, oracle_phi, n_states: int = 100, per_state: int = 40, epochs: int = 4):
+    """The learned preconditioner beside the headline: a network trained in
+    this run on n_states x per_state triples (R, L^-1 R) at 256 x 128 that the
+    library's FP64 solver generates, then used without retraining in the mixed
+    flexible GCR on problem P (zero first guess), against option 3 on the same
+    problem.  Returns the measured solves, iterations and errors."""
+    from paper_2103_16120_gb300 import learned
+    t0 = time.perf_counter()
+    probs = [synth.problem(256, 128, 3_000_000 + s) for s in range(n_states)]
+    rhs = np.stack([synth.random_rhs(256, 128, 3_000_000 + s, per_state) for s in range(n_states)])
+    m = sw.Model()
+    sw.sw_model_set_params(m, learned.init_params(1))
+    x0, tg = learned.make_dataset(m, probs, rhs)
+    B = 32
+    steps = max(1, epochs * x0.shape[0] // B)
+    losses = learned.train(m, x0, tg, steps=steps, batch=B, lr=2e-3, seed=2)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    del x0, tg
+    ny, nx = P["C"].shape
+    g = _grid(sw, torch, P, dev)
+    R = torch.as_tensor(P["R"], device=dev)
+    out = {"training": {"triples": n_states * per_state, "grid": "256x128", "epochs": epochs, "batch": B,
+                        "steps": steps, "final_loss": losses[-1][1] if losses else None,
+                        "data_and_training_s": t_train}}
+    for tag, kw in (("option3", {}), ("learned", {"pc": sw.SW_PC_LEARNED, "model": m})):
+        o = sw.sw_solve_opts_default(k=K_GCR, tol=TOL, prec=sw.SW_PREC_MIXED_FP16, max_iters=6000, **kw)
+        phi = torch.zeros_like(R)
+        st = sw.sw_gcr_solve(g, o, R, phi)         # first call: buffers and network set-up
+        stream = torch.cuda.current_stream()
+        phi.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        st = sw.sw_gcr_solve(g, o, R, phi)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        x = phi.cpu().numpy()
+        out[tag] = {"ms_per_solve": ms, "solves_per_s": 1e3 / ms, "iterations": st.iterations,
+                    "fallbacks": st.fallbacks, "status": int(st.status),
+                    "true_rel_residual": st.true_rel_residual,
+                    "solution_rel_error_vs_fp64_oracle": float(np.linalg.norm(x - oracle_phi) / np.linalg.norm(oracle_phi))}
+    return out
+
+
 def run_gpu(args):
     import torch
     import paper_2103_16120_gb300 as sw
     from paper_2103_16120_gb300 import build as swb
 
+    wl = args.workload
+    q = SEQS[wl]
+    nx, ny, nseq = q["nx"], q["ny"], q["nseq"]
     rank, world, local = dist_env()
     if world > 1:
         import torch.distributed as dist
@@ -225,10 +339,13 @@ def run_gpu(args):
     dev = torch.device("cuda", local)
 
     # --- inputs resident in HBM -------------------------------------------
-    seq = make_sequence(NSEQ)
+    # the sets the run visits (the sequence wraps after nseq solves)
+    nsets = min(nseq, args.warmup + args.steps) if wl == "seq2048" else nseq
+    seq = make_sequence(nsets, wl)
     coeffs = [[torch.as_tensor(P[k], device=dev) for k in KEYS] for P in seq]
     Rs = [torch.as_tensor(P["R"], device=dev) for P in seq]
-    g = sw.sw_grid_create(NX, NY)
+    set_bytes = 8 * nx * ny * 8
+    g = sw.sw_grid_create(nx, ny)
     stream = torch.cuda.current_stream()
 
     stat_bytes = sw.stats_buffer(1).numel()
@@ -236,8 +353,8 @@ def run_gpu(args):
     def run_steps(opts, phi, start, count, sbuf):
         # each step: the coefficients of the step, then the solve, enqueued
         # without a host synchronisation (stats of step i to sbuf slot i)
-        for i, s in enumerate(range(start, start + count)):
-            t = s % NSEQ
+        for i, s_ in enumerate(range(start, start + count)):
+            t = s_ % nsets
             sw.sw_elliptic_set_coeffs(g, *coeffs[t])
             sw.sw_ensemble_solve_async([g], opts, [Rs[t]], [phi], sbuf[i * stat_bytes:(i + 1) * stat_bytes])
 
@@ -248,8 +365,8 @@ def run_gpu(args):
                 raise RuntimeError(f"solve {i} failed: {st.as_dict()}")
         return sts
 
-    def timed(opts, K, W):
-        phi = torch.zeros((NY, NX), dtype=torch.float64, device=dev)
+    def timed(opts, K, W, clk=None):
+        phi = torch.zeros((ny, nx), dtype=torch.float64, device=dev)
         wbuf, sbuf = sw.stats_buffer(max(W, 1)), sw.stats_buffer(K)
         run_steps(opts, phi, 0, W, wbuf)
         torch.cuda.synchronize()
@@ -258,34 +375,35 @@ def run_gpu(args):
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
+        if clk is not None:
+            clk.start()
         ev0.record(stream)
         run_steps(opts, phi, W, K, sbuf)
         ev1.record(stream)
         torch.cuda.synchronize()
+        clocks = clk.stop() if clk is not None else None
         if world > 1:
             torch.distributed.barrier()
         sts = checked(sbuf, K)
         ms = max_over_ranks(ev0.elapsed_time(ev1), world, dev)
-        return ms, sts, phi
+        return ms, sts, clocks
 
-    mixed = sw.sw_solve_opts_default(k=K_GCR, tol=TOL, prec=sw.SW_PREC_MIXED_FP16, max_iters=2000)
-    fp64 = sw.sw_solve_opts_default(k=K_GCR, tol=TOL, prec=sw.SW_PREC_FP64, max_iters=2000)
+    maxit = 6000
+    mixed = sw.sw_solve_opts_default(k=K_GCR, tol=TOL, prec=sw.SW_PREC_MIXED_FP16, max_iters=maxit)
+    fp64 = sw.sw_solve_opts_default(k=K_GCR, tol=TOL, prec=sw.SW_PREC_FP64, max_iters=maxit)
 
     # FP64 reference path first (same steps), then the mixed path with clocks
     ms64, st64, _ = timed(fp64, args.steps, args.warmup)
-    clk = ClockSampler(local)
-    clk.start()
-    msm, stm, phim = timed(mixed, args.steps, args.warmup)
-    clocks = clk.stop()
+    msm, stm, clocks = timed(mixed, args.steps, args.warmup, ClockSampler(local))
 
     # --- kernel-only timing of the solver kernel (dominant kernel) ---------
-    # events around sw_gcr_solve alone: the persistent GCR kernel plus two
-    # tiny state copies
+    # events around sw_gcr_solve alone: the persistent GCR kernel plus one
+    # descriptor kernel and two tiny state copies
     def solver_only(opts, K):
-        phi = torch.zeros((NY, NX), dtype=torch.float64, device=dev)
+        phi = torch.zeros((ny, nx), dtype=torch.float64, device=dev)
         tot, its = 0.0, 0
-        for s in range(K):
-            t = s % NSEQ
+        for s_ in range(K):
+            t = s_ % nsets
             sw.sw_elliptic_set_coeffs(g, *coeffs[t])
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
@@ -296,27 +414,27 @@ def run_gpu(args):
             its += st.iterations
         return tot / K, its / K
 
-    kms, kits = solver_only(mixed, min(args.steps, 50))
+    kms, kits = solver_only(mixed, min(args.steps, 50 if wl == "seq512" else 8))
 
     # --- end to end through host buffers ----------------------------------
-    hcoef = [[torch.as_tensor(P[k]).pin_memory() for k in KEYS] for P in seq[: min(NSEQ, 50)]]
-    hR = [torch.as_tensor(P["R"]).pin_memory() for P in seq[: min(NSEQ, 50)]]
-    hphi = torch.zeros((NY, NX), dtype=torch.float64).pin_memory()
-    dco = [torch.empty((NY, NX), dtype=torch.float64, device=dev) for _ in KEYS]
-    dR = torch.empty((NY, NX), dtype=torch.float64, device=dev)
-    dphi = torch.zeros((NY, NX), dtype=torch.float64, device=dev)
-    n_e2e = min(args.steps, 50)
-
+    n_host = min(nsets, 50 if wl == "seq512" else 4)
+    hcoef = [[torch.as_tensor(P[k]).pin_memory() for k in KEYS] for P in seq[:n_host]]
+    hR = [torch.as_tensor(P["R"]).pin_memory() for P in seq[:n_host]]
+    hphi = torch.zeros((ny, nx), dtype=torch.float64).pin_memory()
+    dco = [torch.empty((ny, nx), dtype=torch.float64, device=dev) for _ in KEYS]
+    dR = torch.empty((ny, nx), dtype=torch.float64, device=dev)
+    dphi = torch.zeros((ny, nx), dtype=torch.float64, device=dev)
+    n_e2e = min(args.steps, 50 if wl == "seq512" else 10)
     ebuf = sw.stats_buffer(max(n_e2e, 3))
 
     def e2e_steps(n):
-        for s in range(n):
-            t = s % len(hR)
+        for s_ in range(n):
+            t = s_ % len(hR)
             for d, h in zip(dco, hcoef[t]):
                 d.copy_(h, non_blocking=True)
             dR.copy_(hR[t], non_blocking=True)
             sw.sw_elliptic_set_coeffs(g, *dco)
-            sw.sw_ensemble_solve_async([g], mixed, [dR], [dphi], ebuf[s * stat_bytes:(s + 1) * stat_bytes])
+            sw.sw_ensemble_solve_async([g], mixed, [dR], [dphi], ebuf[s_ * stat_bytes:(s_ + 1) * stat_bytes])
             hphi.copy_(dphi, non_blocking=True)
         torch.cuda.synchronize()
         checked(ebuf, n)
@@ -326,70 +444,110 @@ def run_gpu(args):
     t0 = time.perf_counter()
     e2e_steps(n_e2e)
     e2e_dt = time.perf_counter() - t0
-    h2d = 8 * NX * NY * 8
-    d2h = NX * NY * 8
+    h2d = set_bytes
+    d2h = nx * ny * 8
 
-    # --- solution error of the mixed path against the FP64 oracle ----------
-    err = None
+    # --- solution error against the FP64 oracle, CPU baseline, learned arm --
+    # every arm solves the sequence's first problem from a zero first guess;
+    # the oracle solves it to 1e-10
+    err = err64 = None
     cpu = None
+    learned_out = None
     if rank == 0:
-        import oracle as O
         import oracle.oracle as orc
         orc.build()
-        last = (args.warmup + args.steps - 1) % NSEQ
-        P = seq[last]
-        ref, _ = O.Problem(P).gcr(P["R"], O.Opts(k=K_GCR, tol=1e-13, max_iters=5000))
-        x = phim.cpu().numpy()
-        err = float(np.linalg.norm(x - ref) / np.linalg.norm(ref))
-        # bounded CPU-oracle sample on the host cores
         cores = cpu_cores()
-        n, dt, its = oracle_solves(seq, 15.0, 200)
-        cpu = {"value": n / dt, "unit": "solves/s", "cores": cores, "kind": "oracle",
-               "sample": f"first {n} solves of the same 512x256 sequence, FP64 oracle, warm start, "
-                         f"OpenMP over rows ({cores} threads), {dt:.1f} s"}
+        os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+        P0 = seq[0]
+        ref, t_or, its_or, its_or_tol = oracle_reference_solve(P0)
+        sw.sw_elliptic_set_coeffs(g, *coeffs[0])
+        for tag, o in (("mixed", mixed), ("fp64", fp64)):
+            phi0 = torch.zeros((ny, nx), dtype=torch.float64, device=dev)
+            st = sw.sw_gcr_solve(g, o, Rs[0], phi0)
+            if st.status != sw.SW_OK:
+                raise RuntimeError(f"{tag} solve of the first problem failed: {st.as_dict()}")
+            e_ = float(np.linalg.norm(phi0.cpu().numpy() - ref) / np.linalg.norm(ref))
+            if tag == "mixed":
+                err = e_
+            else:
+                err64 = e_
+        if wl == "seq512":
+            # bounded CPU-oracle sample on the host cores
+            n, dt, its = oracle_solves(seq, 15.0, 200)
+            cpu = {"value": n / dt, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                   "sample": f"first {n} solves of the same 512x256 sequence, FP64 oracle, warm start, "
+                             f"OpenMP over rows ({cores} threads), {dt:.1f} s"}
+        else:
+            v_or = its_or / (t_or * its_or_tol)
+            cpu = {"value": v_or, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                   "sample": f"one FP64 oracle solve of the sequence's first 2048x1024 problem from zero, "
+                             f"{its_or} iterations to 1e-10 in {t_or:.1f} s, scaled to the {its_or_tol} "
+                             f"iterations that reach 1e-8; OpenMP over rows ({cores} threads)"}
+            if not args.no_learned:
+                learned_out = learned_arm(sw, torch, dev, P0, ref)
+                m3, ml = learned_out["option3"], learned_out["learned"]
+                learned_out["gain_vs_option3"] = m3["ms_per_solve"] / ml["ms_per_solve"]
+                learned_out["shipped"] = "learned" if ml["ms_per_solve"] < m3["ms_per_solve"] else "option3"
+                if learned_out["shipped"] == "option3":
+                    learned_out["reason"] = (
+                        "the learned directions cost more than they save: each network turn ends the persistent "
+                        "launch and round-trips through the host, and the network's +-15-point receptive field "
+                        "cannot represent the coupling around whole latitude circles that option 3 solves "
+                        "exactly; the headline is the mixed-precision solver with option 3")
 
-    its_m = float(np.mean([s.iterations for s in stm]))
-    its_64 = float(np.mean([s.iterations for s in st64]))
+    its_m = float(np.mean([s_.iterations for s_ in stm]))
+    its_64 = float(np.mean([s_.iterations for s_ in st64]))
     value = world * args.steps / (msm / 1e3)
     v64 = world * args.steps / (ms64 / 1e3)
     bpp = algorithmic_bytes_per_point(True, kits)
-    achieved = bpp * NX * NY / (kms / 1e3) / 1e9
+    achieved = bpp * nx * ny / (kms / 1e3) / 1e9
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
     peak = peaks.get("hbm_gbs", 6800.0)
+    if wl == "seq512":
+        traffic = TRAFFIC["seq512"]
+        note = ("algorithmic bytes of one solve / solver time; working set is L2-resident "
+                "and the solve is grid-barrier-latency bound at this size")
+    else:
+        tpi = TRAFFIC["seq2048_per_iteration"]
+        traffic = tpi * kits if tpi else None
+        note = ("algorithmic bytes of one solve / solver time (persistent kernel, mean iterations of the "
+                "measured launches); traffic: ncu DRAM bytes per iteration of one launch times those iterations")
     launches_per_step = 4   # k_faces, k_factor<float>, k_init_one, k_gcr
     if rank == 0:
-        print(json.dumps({
+        line = {
             "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": msm / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 (f16 storage, f64 reductions)",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "nx": NX, "ny": NY, "tol": TOL, "k": K_GCR,
-                       "preconditioner": "semi-implicit Richardson, 2 iterations",
-                       "precision": "mixed-fp16", "l2": "inputs larger than L2 (200 resident coefficient sets, 1.7 GB)",
+            "config": {"workload": q["label"], "nx": nx, "ny": ny, "tol": TOL, "k": K_GCR,
+                       "preconditioner": "semi-implicit Richardson, 2 iterations (option 3); learned arm beside",
+                       "precision": "mixed-fp16",
+                       "l2": f"inputs larger than L2 ({nsets} resident coefficient sets, {nsets * set_bytes / 1e9:.1f} GB)",
                        "parallelism": f"replicas x{world}"},
             "fp64_gcr": {"value": v64, "unit": "solves/s", "ms_per_step": ms64 / args.steps,
-                         "mean_iterations": its_64},
+                         "mean_iterations": its_64, "solution_rel_error_vs_fp64_oracle": err64},
             "speedup_vs_fp64": value / v64,
             "mean_iterations": its_m,
             "solution_rel_error_vs_fp64_oracle": err,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": TRAFFIC_512,
-                         "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch, "
-                                           "profiles/k_gcr_f16_seq512x256.md",
+                         "frac": achieved / peak, "traffic": traffic,
                          "kernel": "k_gcr<PolF16> (persistent GCR)",
-                         "note": "algorithmic bytes of one solve / solver time; working set is L2-resident "
-                                 "and the solve is grid-barrier-latency bound at this size",
-                         "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback"},
+                         "kernel_ms_per_launch": kms, "kernel_mean_iterations": kits,
+                         "algorithmic_bytes_per_point": bpp, "note": note,
+                         "peak_source": "measured hbm_gbs (of measured)" if peaks else "fallback 6800 GB/s"},
             "cpu_baseline": cpu,
             "e2e": {"value": world * n_e2e / e2e_dt, "unit": "solves/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clocks,
-        }), flush=True)
+        }
+        if learned_out is not None:
+            line["learned"] = learned_out
+        print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
 
@@ -588,64 +746,6 @@ def run_ensemble(args):
     }), flush=True)
 
 
-def run_large(args):
-    import torch
-    import paper_2103_16120_gb300 as sw
-    from paper_2103_16120_gb300 import build as swb
-    swb.build()
-    dev = torch.device("cuda", 0)
-    nx, ny = 2048, 1024
-    n = args.warmup + args.steps
-    seq = [synth.sequence_problem(nx, ny, 4000, t) for t in range(n)]
-    g = sw.sw_grid_create(nx, ny)
-    stream = torch.cuda.current_stream()
-    res = {}
-    for tag, prec in (("fp64", sw.SW_PREC_FP64), ("mixed", sw.SW_PREC_MIXED_FP16)):
-        o = sw.sw_solve_opts_default(k=K_GCR, tol=TOL, prec=prec, max_iters=4000)
-        phi = torch.zeros((ny, nx), dtype=torch.float64, device=dev)
-        tot, its, sol = 0.0, 0, None
-        for t, P in enumerate(seq):
-            sw.sw_elliptic_set_coeffs(g, *[torch.as_tensor(P[k], device=dev) for k in KEYS])
-            R = torch.as_tensor(P["R"], device=dev)
-            torch.cuda.synchronize()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            st = sw.sw_gcr_solve(g, o, R, phi)
-            b.record(stream)
-            torch.cuda.synchronize()
-            if st.status != sw.SW_OK:
-                raise RuntimeError(f"solve failed: {st.as_dict()}")
-            if t >= args.warmup:
-                tot += a.elapsed_time(b)
-                its += st.iterations
-        res[tag] = {"ms_per_solve": tot / args.steps, "solves_per_s": 1e3 * args.steps / tot,
-                    "mean_iterations": its / args.steps, "phi": phi}
-    # reference for the error: the FP64 GPU solve of the last problem to 1e-13
-    o = sw.sw_solve_opts_default(k=K_GCR, tol=1e-13, prec=sw.SW_PREC_FP64, max_iters=8000)
-    ref = res["fp64"]["phi"].clone()
-    sw.sw_gcr_solve(g, o, torch.as_tensor(seq[-1]["R"], device=dev), ref)
-    err = float(torch.linalg.norm(res["mixed"]["phi"] - ref) / torch.linalg.norm(ref))
-    mixed = res["mixed"]
-    bpp = algorithmic_bytes_per_point(True, mixed["mean_iterations"])
-    achieved = bpp * nx * ny / (mixed["ms_per_solve"] * 1e-3) / 1e9
-    peak = _peaks().get("hbm_gbs", 6800.0)
-    print(json.dumps({
-        "metric": METRIC, "value": mixed["solves_per_s"], "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": mixed["ms_per_solve"], "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32 (f16 storage, f64 reductions)", "data": "synthetic",
-        "config": {"workload": "2048x1024 solve sequence, warm start", "tol": TOL, "k": K_GCR},
-        "fp64_gcr": {k: v for k, v in res["fp64"].items() if k != "phi"},
-        "mixed": {k: v for k, v in mixed.items() if k != "phi"},
-        "speedup_vs_fp64": mixed["solves_per_s"] / res["fp64"]["solves_per_s"],
-        "solution_rel_error_vs_fp64_gpu_1e-13": err,
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "kernel": "k_gcr<PolF16>",
-                     "note": "algorithmic bytes of one solve / solve time",
-                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
-        "cpu_baseline": None, "gpu_launches": 3 * args.steps,
-    }), flush=True)
-
-
 # bytes per cell of one model step moved by the kernels around the solves
 # (fields of 8 bytes unless noted): forcing 9 in / 7 out; transport 4 / 2;
 # per pass (two passes): coefficients 10-11 / 11, face coefficients 7 / 8 plus
@@ -815,11 +915,12 @@ def run_oracle_timings(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gcr", choices=["gcr", "reference"])
-    ap.add_argument("--workload", default="seq512",
-                    choices=["seq512", "learned256", "ensemble64", "large2048", "swe512", "oracle"])
+    ap.add_argument("--workload", default="seq2048",
+                    choices=["seq2048", "seq512", "learned256", "ensemble64", "swe512", "oracle"])
+    ap.add_argument("--no-learned", action="store_true", help="seq2048: leave the learned arm out")
     ap.add_argument("--samples", type=int, default=20000, help="learned256: training triples")
     ap.add_argument("--epochs", type=int, default=4, help="learned256: training epochs")
     args = ap.parse_args()
@@ -831,8 +932,6 @@ def main():
         run_learned(args)
     elif args.workload == "ensemble64":
         run_ensemble(args)
-    elif args.workload == "large2048":
-        run_large(args)
     elif args.workload == "swe512":
         run_swe(args)
     elif args.workload == "oracle":

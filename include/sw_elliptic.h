@@ -279,10 +279,13 @@ sw_status sw_model_target(sw_model m, sw_grid g, const float *r, const float *e,
  *    example, calls from two host threads or calls on two streams.  Issue
  *    them one after another.  Each call waits for its own solve on `stream`
  *    before it returns.
- *  - The first call on each device looks up the scratch's device address.
- *    That is a one-time setup step and may load the library's device code.
- *    Make this first call, with that device current, before any stream
- *    capture begins. */
+ *  - Every call looks up the scratch's device address in the current
+ *    context (it can move when a context is destroyed and created again).
+ *    The first call on a device may also load the library's device code, a
+ *    one-time setup step: make this first call, with that device current,
+ *    before any stream capture begins.
+ *  - The launch shape is the one sw_gcr_solve picks for the same grid and
+ *    options, so the two give the same results. */
 sw_status sw_gcr_solve_noalloc(sw_grid g, const sw_solve_opts *o, const double *R, double *phi,
                                sw_solve_stats *stats, void *stream);
 

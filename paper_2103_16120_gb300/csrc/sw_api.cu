@@ -832,39 +832,12 @@ extern "C" sw_status sw_gcr_solve_noalloc(sw_grid g, const sw_solve_opts *o, con
     CK(cudaMemsetAsync(&g->blk->g, 0, sizeof(GlobalCtl), s));
     if (o->res_history) CK(launch_fill(o->res_history, (size_t)o->max_iters + 1, NAN, s));
 
-    // launch shape of a one-member solve: a block per row when they can all
-    // be resident (with as much of the row cached as fits), else as many
-    // blocks as can be resident, each cycling over rows
-    const int threads = row_threads(g->nx, o->threads_per_row);
-    int grid = 0, cc = 0, cs = 0;
-    size_t smem = 0;
-    const int levels[3][2] = {{1, 1}, {1, 0}, {0, 0}};
-    for (int lv = 0; lv < 3 && !grid; ++lv) {
-        const size_t sm_l = gcr_smem_bytes(o->prec, g->nx, o->k, levels[lv][0], levels[lv][1]);
-        int bps = 0;
-        CK(gcr_occupancy(o->prec, o->k, 1, threads, sm_l, &bps));
-        if (bps > 0 && g->ny <= bps * g->sms) {
-            grid = g->ny; cc = levels[lv][0]; cs = levels[lv][1]; smem = sm_l;
-        }
-    }
-    if (!grid) {
-        smem = gcr_smem_bytes(o->prec, g->nx, o->k, 0, 0);
-        int bps = 0;
-        CK(gcr_occupancy(o->prec, o->k, 1, threads, smem, &bps));
-        if (bps < 1) return fail(SW_ERR_INVALID_ARG, "sw_gcr_solve_noalloc: grid rows too long for the solver kernel");
-        grid = std::min(bps * g->sms, g->ny);
-    }
-    EnsDesc &D = *g->h_desc;
-    D.n = 1;
-    D.grid = grid;
-    D.cache_const = cc;
-    D.cache_state = cs;
-    D.stats = nullptr;
-    D.cta_begin[0] = 0;
-    D.cta_begin[1] = grid;
-    D.blk[0] = g->blk;
-    CK(cudaMemcpyAsync(g->desc, &D, sizeof(EnsDesc), cudaMemcpyHostToDevice, s));
-    CK(launch_gcr(o->prec, o->k, 1, g->desc, grid, g->nx, threads, smem, s));
+    // the launch shape of sw_gcr_solve for this grid and these options
+    Plan P;
+    if ((st = plan_launch(1, &g, o, g->nx, P))) return st;
+    fill_desc(*g->h_desc, 1, &g, P);
+    CK(cudaMemcpyAsync(g->desc, g->h_desc, sizeof(EnsDesc), cudaMemcpyHostToDevice, s));
+    CK(launch_gcr(o->prec, o->k, P.minb, g->desc, P.grid, g->nx, P.threads, P.smem, s));
     CK(cudaMemcpyAsync(g->h_ctl, &g->blk->ctl, sizeof(MemberCtl) + sizeof(GlobalCtl), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(g->h_eta, g->eta, sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));

@@ -3,8 +3,6 @@
 // the module is loaded, not through a runtime allocation.  It sits in a file
 // of its own so that, with lazy module loading, only programs that use the
 // no-allocation solve load it.
-#include <mutex>
-
 #include "../../include/sw_elliptic.h"
 #include "sw_internal.h"
 
@@ -12,27 +10,19 @@ namespace sw {
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[SW_NOALLOC_SCRATCH_BYTES];
 
-constexpr int NOALLOC_MAX_DEVICES = 64;
-
+// The device address of the scratch in the current context.  Host code only
+// holds a stand-in for the array, so the address is asked of the runtime on
+// every call: a context that was torn down and created again (a device reset,
+// a released and re-retained primary context) reloads the module, and the
+// array may then sit elsewhere.  The lookup allocates nothing.
 cudaError_t noalloc_scratch(void **ptr, size_t *bytes)
 {
-    static std::mutex mu;
-    static void *addr[NOALLOC_MAX_DEVICES] = {};
     *ptr = nullptr;
     *bytes = SW_NOALLOC_SCRATCH_BYTES;
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(mu);
-    if (!addr[dev]) {
-        // once per device, with that device current
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        addr[dev] = p;
-    }
-    *ptr = addr[dev];
+    *ptr = p;
     return cudaSuccess;
 }
 

@@ -62,6 +62,30 @@ def test_matches_gcr_solve_on_two_calls_in_a_row(nx, ny, prec):
         assert abs(st.true_rel_residual - st_ref.true_rel_residual) <= 1e-14
 
 
+def test_matches_gcr_solve_when_blocks_own_several_rows():
+    """512 rows of 512 points with 256 threads per row are more rows than the
+    device holds resident blocks, so every block cycles over several rows and
+    the launch may take the two-blocks-per-SM kernel.  The scratch call must
+    take the same launch shape as sw_gcr_solve."""
+    nx, ny = 512, 512
+    P = synth.problem(nx, ny, 4500)
+    g_ref, g = grid_with(P, nx, ny), grid_with(P, nx, ny)
+    o = sw.sw_solve_opts_default(prec=sw.SW_PREC_MIXED_FP16, tol=1e-8, k=2, threads_per_row=256)
+    assert sw.sw_grid_workspace_bytes(g, o) <= sw.SW_NOALLOC_SCRATCH_BYTES
+    props = torch.cuda.get_device_properties(0)
+    assert ny > 2 * props.multi_processor_count
+    Rd = dev(P["R"])
+    for _ in range(2):
+        ref = torch.zeros_like(Rd)
+        st_ref = sw.sw_gcr_solve(g_ref, o, Rd, ref)
+        phi = torch.zeros_like(Rd)
+        st = sw.sw_gcr_solve_noalloc(g, o, Rd, phi)
+        torch.cuda.synchronize()
+        assert st.status == st_ref.status == sw.SW_OK
+        assert st.iterations == st_ref.iterations
+        assert rel(phi, ref) <= TOL
+
+
 def test_allocates_no_device_memory():
     nx, ny = 512, 256
     P = synth.problem(nx, ny, 4300)
