@@ -108,6 +108,15 @@ typedef struct {
                             ||r||^2 than fb_ratio times the share the last
                             option-3 direction removed (or is not finite);
                             default 0.5 */
+    int row_mode;        /* launch shape of the solver kernel: 0 automatic (one
+                            thread block per latitude row while the rows fit the
+                            resident blocks, else one warp per row when nx is a
+                            power of two >= 128 and a single grid is solved
+                            without the learned preconditioner, else blocks
+                            cycling over rows); 1 thread blocks only; 2 one warp
+                            per row (SW_ERR_INVALID_ARG where not possible).
+                            The results agree to rounding: the inner products
+                            sum in another order. */
 } sw_solve_opts;
 
 typedef struct {
@@ -125,7 +134,7 @@ typedef struct {
 /* Fills *o with the defaults: k = 4, tol = 1e-8, max_iters = 1000,
  * min_iters = 0, option 3 with 2 Richardson iterations, automatic eta,
  * omega = 1, FP64, automatic pole band, no periodic true residual, no model,
- * fb_ratio = 0.5. */
+ * fb_ratio = 0.5, automatic row mode. */
 void sw_solve_opts_default(sw_solve_opts *o);
 
 /* Create a grid of nx x ny points on a sphere of the given radius (m).

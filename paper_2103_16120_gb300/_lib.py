@@ -40,7 +40,7 @@ class SolveOpts(C.Structure):
                 ("prec", C.c_int), ("pole_band_rows", C.c_int), ("ru_every", C.c_int),
                 ("threads_per_row", C.c_int),
                 ("res_history", C.c_void_p), ("row_residual", C.c_void_p),
-                ("model", C.c_void_p), ("fb_ratio", C.c_double)]
+                ("model", C.c_void_p), ("fb_ratio", C.c_double), ("row_mode", C.c_int)]
 
 
 class SolveStats(C.Structure):

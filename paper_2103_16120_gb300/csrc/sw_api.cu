@@ -45,6 +45,10 @@ struct sw_grid_s {
     double *gam32, *ec32;          // per row, of the FP32 zonal factors
     bool f64_valid;                // the FP64 zonal factors match the coefficients and eta
     float *wax, *wcx, *wbx, *way, *wcy, *wby, *wC, *wdiag, *lf32, *invD32, *zz32;
+    // the zonal factors transposed per row for the warp-per-row solver (rows
+    // of a power of two of at least 128 points; null otherwise)
+    double *lfT, *invDT, *zzT;
+    float *lf32T, *invD32T, *zz32T;
     bool has_coeffs;
     double eta_explicit;           // > 0 when chosen by sw_grid_set_eta
     // solver workspace
@@ -126,7 +130,8 @@ extern "C" sw_status sw_grid_create(int nx, int ny, double radius, sw_grid *out)
     cudaError_t e = cudaGetDevice(&g->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, g->device);
     size_t N = g->N;
-    size_t bytes = 11 * al(N * 8) + 5 * al((size_t)ny * 8) + al(8) + 11 * al(N * 4);
+    const bool wt = warp_rows_ok(nx);
+    size_t bytes = 11 * al(N * 8) + 5 * al((size_t)ny * 8) + al(8) + 11 * al(N * 4) + (wt ? 3 * (al(N * 8) + al(N * 4)) : 0);
     if (e == cudaSuccess) e = cudaMalloc(&g->cmem, bytes);
     if (e == cudaSuccess) e = cudaMalloc((void **)&g->blk, sizeof(SolverBlock));
     if (e == cudaSuccess) e = cudaMalloc((void **)&g->desc, sizeof(EnsDesc));
@@ -161,6 +166,10 @@ extern "C" sw_status sw_grid_create(int nx, int ny, double radius, sw_grid *out)
     g->eta = (double *)p; p += al(8);
     float **d32[] = {&g->wax, &g->wcx, &g->wbx, &g->way, &g->wcy, &g->wby, &g->wC, &g->wdiag, &g->lf32, &g->invD32, &g->zz32};
     for (auto q : d32) { *q = (float *)p; p += al(N * 4); }
+    if (wt) {
+        for (auto q : {&g->lfT, &g->invDT, &g->zzT}) { *q = (double *)p; p += al(N * 8); }
+        for (auto q : {&g->lf32T, &g->invD32T, &g->zz32T}) { *q = (float *)p; p += al(N * 4); }
+    }
     *out = g;
     return SW_OK;
 }
@@ -231,6 +240,7 @@ static sw_status check_opts(const sw_solve_opts *o, bool solve)
     if (o->threads_per_row < 0 || o->threads_per_row > MAX_THREADS || (o->threads_per_row & 31))
         return fail(SW_ERR_INVALID_ARG, "threads_per_row must be 0 or a multiple of 32 up to 256");
     if (!std::isfinite(o->eta)) return fail(SW_ERR_INVALID_ARG, "eta must be finite");
+    if (o->row_mode < 0 || o->row_mode > 2) return fail(SW_ERR_INVALID_ARG, "row_mode must be 0, 1 or 2");
     return SW_OK;
 }
 
@@ -279,6 +289,8 @@ static FactorArgs factor_args(const sw_grid_s *g)
     f.ax = g->ax; f.C = g->C; f.rowmax = g->rowmax;
     f.lf = g->lf; f.invD = g->invD; f.zz = g->zz; f.gam = g->gam; f.ec = g->ec; f.eta_out = g->eta;
     f.lf32 = g->lf32; f.invD32 = g->invD32; f.zz32 = g->zz32; f.gam32 = g->gam32; f.ec32 = g->ec32;
+    f.lfT = g->lfT; f.invDT = g->invDT; f.zzT = g->zzT;
+    f.lf32T = g->lf32T; f.invD32T = g->invD32T; f.zz32T = g->zz32T;
     return f;
 }
 
@@ -400,11 +412,13 @@ static void fill_member(sw_grid g, const sw_solve_opts *o, const double *R, doub
         M.way = (const ct *)g->way; M.wcy = (const ct *)g->wcy; M.wby = (const ct *)g->wby;
         M.wC = (const ct *)g->wC; M.wdiag = (const ct *)g->wdiag;
         M.lf = (const ft *)g->lf32; M.invD = (const ft *)g->invD32; M.zz = (const ft *)g->zz32;
+        M.lfT = (const ft *)g->lf32T; M.invDT = (const ft *)g->invD32T; M.zzT = (const ft *)g->zz32T;
     } else {
         M.wax = (const ct *)g->ax; M.wcx = (const ct *)g->cx; M.wbx = (const ct *)g->bx;
         M.way = (const ct *)g->ay; M.wcy = (const ct *)g->cy; M.wby = (const ct *)g->by;
         M.wC = (const ct *)g->C; M.wdiag = (const ct *)g->diag;
         M.lf = (const ft *)g->lf; M.invD = (const ft *)g->invD; M.zz = (const ft *)g->zz;
+        M.lfT = (const ft *)g->lfT; M.invDT = (const ft *)g->invDT; M.zzT = (const ft *)g->zzT;
     }
     if constexpr (Pol::kMixed) { M.gam = g->gam32; M.ec = g->ec32; }
     else { M.gam = g->gam; M.ec = g->ec; }
@@ -498,7 +512,7 @@ extern "C" sw_status sw_precond_apply(sw_grid g, const sw_solve_opts *o, const v
 // linearly with the resolution) and cycle over several rows each, with
 // everything in global memory.
 struct Plan {
-    int grid = 0, cc = 0, cs = 0, threads = 0, minb = 1;
+    int grid = 0, cc = 0, cs = 0, threads = 0, minb = 1, warp = 0;
     size_t smem = 0;
     std::vector<int> nb;
 };
@@ -513,13 +527,48 @@ static sw_status plan_launch(int n, const sw_grid *grids, const sw_solve_opts *o
     for (int m = 0; m < n; ++m) rows_total += grids[m]->ny;
     // the learned preconditioner ends a launch before every application of
     // the network, so the owner-only vectors cannot live in shared memory
-    for (int lv = (o->pc == SW_PC_LEARNED ? 1 : 0); lv < 3 && !P.grid; ++lv) {
+    const bool warp_possible = n == 1 && o->pc != SW_PC_LEARNED && grids[0]->lfT;
+    if (o->row_mode == 2 && !warp_possible)
+        return fail(SW_ERR_INVALID_ARG, "row_mode 2 (one warp per row) needs one grid with nx a power of two >= 128 "
+                                        "and a preconditioner other than the learned one");
+    for (int lv = (o->pc == SW_PC_LEARNED ? 1 : 0); lv < 3 && !P.grid && o->row_mode != 2; ++lv) {
         const size_t sm_l = gcr_smem_bytes(o->prec, max_nx, o->k, levels[lv][0], levels[lv][1]);
         int bps = 0;
-        CK(gcr_occupancy(o->prec, o->k, 1, P.threads, sm_l, &bps));
+        CK(gcr_occupancy(o->prec, o->k, 1, 0, P.threads, sm_l, &bps));
         if (bps > 0 && rows_total <= (long)bps * sms) {
             for (int m = 0; m < n; ++m) P.nb[m] = grids[m]->ny;
             P.grid = (int)rows_total; P.cc = levels[lv][0]; P.cs = levels[lv][1]; P.smem = sm_l;
+        }
+    }
+    if (!P.grid && warp_possible && o->row_mode != 1) {
+        // more rows than resident blocks, rows of a power of two of at least
+        // 128 points: one warp per row (every SM works on as many rows at once
+        // as it holds warps), on every SM
+        P.threads = MAX_THREADS;
+        P.smem = gcr_warp_smem_bytes(o->prec, max_nx, P.threads);
+        P.cc = P.cs = 0;
+        int bps = 0, bps2 = 0;
+        CK(gcr_occupancy(o->prec, o->k, 1, 1, P.threads, P.smem, &bps));
+        CK(gcr_occupancy(o->prec, o->k, 2, 1, P.threads, P.smem, &bps2));
+        const int warps = P.threads / 32;
+        const int need = (grids[0]->ny + warps - 1) / warps;   // blocks that give every row its own warp
+        // the register budget of one block per SM unless that leaves rows
+        // without a warp and two blocks fit
+        P.minb = 1;
+        if (bps * sms < need && bps2 > bps) { bps = bps2; P.minb = 2; }
+        if (bps >= 1) {
+            // the same number of blocks on every SM, as few as give every row a
+            // warp, and no more blocks than rows (the block partial sums are
+            // kept per row slot)
+            const int per_sm = std::min(bps, std::max(1, (need + sms - 1) / sms));
+            P.grid = std::min(per_sm * sms, grids[0]->ny);
+            P.nb[0] = P.grid;
+            P.warp = 1;
+        } else if (o->row_mode == 2) {
+            return fail(SW_ERR_INVALID_ARG, "row_mode 2: the warp-per-row kernel does not fit this device");
+        } else {
+            P.threads = row_threads(max_nx, o->threads_per_row);
+            P.minb = 1;
         }
     }
     if (!P.grid) {
@@ -528,8 +577,8 @@ static sw_status plan_launch(int n, const sw_grid *grids, const sw_solve_opts *o
         P.smem = gcr_smem_bytes(o->prec, max_nx, o->k, 0, 0);
         P.cc = P.cs = 0;
         int bps = 0, bps2 = 0;
-        CK(gcr_occupancy(o->prec, o->k, 1, P.threads, P.smem, &bps));
-        CK(gcr_occupancy(o->prec, o->k, 2, P.threads, P.smem, &bps2));
+        CK(gcr_occupancy(o->prec, o->k, 1, 0, P.threads, P.smem, &bps));
+        CK(gcr_occupancy(o->prec, o->k, 2, 0, P.threads, P.smem, &bps2));
         if (bps2 > bps) { bps = bps2; P.minb = 2; }
         if (bps < 1) return fail(SW_ERR_INVALID_ARG, "grid rows too long for the solver kernel");
         const int cap = bps * sms;
@@ -559,6 +608,7 @@ static void fill_desc(EnsDesc &D, int n, const sw_grid *grids, const Plan &P, sw
     D.grid = P.grid;
     D.cache_const = P.cc;
     D.cache_state = P.cs;
+    D.warp_rows = P.warp;
     D.cta_begin[0] = 0;
     for (int m = 0; m < n; ++m) {
         D.cta_begin[m + 1] = D.cta_begin[m] + P.nb[m];
@@ -626,8 +676,9 @@ static sw_status solve_one_async(sw_grid g, const sw_solve_opts *o, const double
     a.nb0 = P.nb[0];
     a.cache_const = P.cc;
     a.cache_state = P.cs;
+    a.warp_rows = P.warp;
     CK(launch_init_one(a, s));
-    CK(launch_gcr(o->prec, o->k, P.minb, g->desc, P.grid, max_nx, P.threads, P.smem, s));
+    CK(launch_gcr(o->prec, o->k, P.minb, P.warp, g->desc, P.grid, max_nx, P.threads, P.smem, s));
     return SW_OK;
 }
 
@@ -694,7 +745,7 @@ static sw_status solve_members(int n, const sw_grid *grids, const sw_solve_opts 
     EnsDesc &D = *lead->h_desc;
     fill_desc(D, n, grids, P);
     CK(cudaMemcpyAsync(lead->desc, &D, sizeof(EnsDesc), cudaMemcpyHostToDevice, s));
-    CK(launch_gcr(o->prec, o->k, P.minb, lead->desc, grid, max_nx, threads, smem, s));
+    CK(launch_gcr(o->prec, o->k, P.minb, P.warp, lead->desc, grid, max_nx, threads, smem, s));
     if (o->pc == SW_PC_LEARNED) {
         // flexible GCR: a launch ends where the next direction is the
         // network's; the network runs on r, its output becomes e, and the
@@ -710,7 +761,7 @@ static sw_status solve_members(int n, const sw_grid *grids, const sw_solve_opts 
             if ((st = model_precondition(o->model, g, r, o->prec == SW_PREC_FP64, ef, s))) return st;
             CK(launch_store_e(o->prec, g->blk->dev, ef, g->nx, g->ny, row_threads(g->nx, o->threads_per_row), s));
             CK(cudaMemsetAsync(&g->blk->g, 0, sizeof(GlobalCtl), s));
-            CK(launch_gcr(o->prec, o->k, P.minb, lead->desc, grid, max_nx, threads, smem, s));
+            CK(launch_gcr(o->prec, o->k, P.minb, P.warp, lead->desc, grid, max_nx, threads, smem, s));
         }
     }
     return finish_members(n, grids, stats, s);
@@ -837,7 +888,7 @@ extern "C" sw_status sw_gcr_solve_noalloc(sw_grid g, const sw_solve_opts *o, con
     if ((st = plan_launch(1, &g, o, g->nx, P))) return st;
     fill_desc(*g->h_desc, 1, &g, P);
     CK(cudaMemcpyAsync(g->desc, g->h_desc, sizeof(EnsDesc), cudaMemcpyHostToDevice, s));
-    CK(launch_gcr(o->prec, o->k, P.minb, g->desc, P.grid, g->nx, P.threads, P.smem, s));
+    CK(launch_gcr(o->prec, o->k, P.minb, P.warp, g->desc, P.grid, g->nx, P.threads, P.smem, s));
     CK(cudaMemcpyAsync(g->h_ctl, &g->blk->ctl, sizeof(MemberCtl) + sizeof(GlobalCtl), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(g->h_eta, g->eta, sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -933,7 +984,7 @@ extern "C" sw_status sw_ensemble_solve_async(int n, const sw_grid *grids, const 
         }
     }
     CK(launch_init_members(lead->desc, n, s));
-    CK(launch_gcr(o->prec, o->k, P.minb, lead->desc, P.grid, max_nx, P.threads, P.smem, s));
+    CK(launch_gcr(o->prec, o->k, P.minb, P.warp, lead->desc, P.grid, max_nx, P.threads, P.smem, s));
     return SW_OK;
 }
 

@@ -106,6 +106,9 @@ struct MemberDev {
     // zonal factors of T = I - eta (P^Z - P^H): multipliers, inverse pivots,
     // Sherman-Morrison vector; per row gamma and the wrap coupling
     const fac_t *lf, *invD, *zz;
+    // the same factors transposed per row for the warp-per-row path: point i
+    // of a row at (i % m) * 32 + i / m, m = nx / 32 (null when not stored)
+    const fac_t *lfT, *invDT, *zzT;
     const double *gam, *ec;
     // solve fields
     const double *R;
@@ -158,17 +161,25 @@ struct InitOneArgs {
     SolverBlock *blk;
     struct EnsDesc *desc;
     sw_solve_stats *stats;
-    int grid, nb0, cache_const, cache_state;
+    int grid, nb0, cache_const, cache_state, warp_rows;
 };
 
 // members of one persistent launch and their block ranges
 struct EnsDesc {
     int n, grid;
     int cache_const, cache_state;   // row constants / owner-only vectors in shared memory
+    int warp_rows, pad_;            // one warp per latitude row (sw_warp.cuh) instead of one block
     sw_solve_stats *stats;          // device, n entries, or null: each member's stats at the end
     int cta_begin[MAX_MEMBERS + 1];
     SolverBlock *blk[MAX_MEMBERS];
 };
+
+// rows one warp can own in the warp-per-row solver (sw_warp.cuh): a power of
+// two of 128 .. MAX_NX points
+__host__ __device__ inline bool warp_rows_ok(int nx) { return nx >= 128 && nx <= MAX_NX && (nx & (nx - 1)) == 0; }
+
+// physical slot of the cycle's logical direction l (restarts rotate the base)
+__device__ __forceinline__ int phys_slot(const MemberCtl &c, int k, int l) { return (c.base + l) % (k + 1); }
 
 // ---------------------------------------------------------------------------
 // block-level helpers (blockDim.x a multiple of 32, <= MAX_THREADS)

@@ -37,6 +37,10 @@ struct FactorArgs {
     double *lf, *invD, *zz, *gam, *ec, *eta_out;        // FP64 factors
     float *lf32, *invD32, *zz32;                         // FP32 factors
     double *gam32, *ec32;                                // per row, of the FP32 factors
+    // the factors transposed per row for the warp-per-row solver (or null):
+    // point i at (i % m) * 32 + i / m, m = nx / 32
+    double *lfT, *invDT, *zzT;
+    float *lf32T, *invD32T, *zz32T;
 };
 
 // geometry of a grid handle, for translation units outside sw_api.cu
@@ -49,9 +53,25 @@ GridGeom grid_geom(const ::sw_grid_s *g);
 cudaError_t launch_faces(const FaceArgs &a, int threads, cudaStream_t s);
 cudaError_t launch_factor(const FactorArgs &a, bool fp64, int threads, cudaStream_t s);
 size_t gcr_smem_bytes(int prec, int max_nx, int k, int cache_const, int cache_state);
-cudaError_t gcr_occupancy(int prec, int k, int minb, int threads, size_t smem, int *blocks_per_sm);
-cudaError_t launch_gcr(int prec, int k, int minb, const EnsDesc *Ddev, int grid, int max_nx, int threads,
+// shared memory of the warp-per-row mode (0 when nx does not allow it)
+size_t gcr_warp_smem_bytes(int prec, int nx, int threads);
+cudaError_t gcr_occupancy(int prec, int k, int minb, int warp, int threads, size_t smem, int *blocks_per_sm);
+cudaError_t launch_gcr(int prec, int k, int minb, int warp, const EnsDesc *Ddev, int grid, int max_nx, int threads,
                        size_t smem, cudaStream_t s);
+// the instantiations of the GCR kernel, one translation unit each
+// (sw_gcr_*.cu): the kernel for a k and register budget, and the unit's
+// barrier test hook and time line
+#define SW_GCR_UNIT_DECL(TAG)                                                              \
+    const void *gcr_kernel_##TAG(int k, int minb);                                         \
+    cudaError_t gcr_debug_##TAG(unsigned long long extra, unsigned long long limit_ns);    \
+    void gcr_trace_##TAG(unsigned long long *buf, int cap, int block);
+SW_GCR_UNIT_DECL(f64)
+SW_GCR_UNIT_DECL(f16)
+SW_GCR_UNIT_DECL(bf16)
+SW_GCR_UNIT_DECL(w64)
+SW_GCR_UNIT_DECL(w16)
+SW_GCR_UNIT_DECL(wbf16)
+SW_GCR_UNIT_DECL(solver)
 cudaError_t launch_operator_f64(const OpArgs<double> &a, const double *x, double *y, int threads, cudaStream_t s);
 cudaError_t launch_operator_f32(const OpArgs<float> &a, const float *x, float *y, int threads, cudaStream_t s);
 cudaError_t launch_precond(int prec, const void *Mdev, int nx, int ny, int nstages, void *qout, int threads,

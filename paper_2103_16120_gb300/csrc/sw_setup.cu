@@ -189,6 +189,12 @@ __global__ void __launch_bounds__(MAX_THREADS) k_factor(FactorArgs a)
     T Dprev = (c0 > 0) ? Q.m00 / Q.m10 : T(0);
     double *lf64 = a.lf + row, *iD64 = a.invD + row;
     float *lf32 = a.lf32 + row, *iD32 = a.invD32 + row;
+    // the transposed copies of the warp-per-row solver: point i at
+    // (i % m) * 32 + i / m of the row, m = nx / 32 (nx a power of two)
+    T *lfT = f64 ? (T *)a.lfT : (T *)a.lf32T, *iDT = f64 ? (T *)a.invDT : (T *)a.invD32T;
+    T *zT = f64 ? (T *)a.zzT : (T *)a.zz32T;
+    const int mT = nx >> 5, lmT = mT > 0 ? __ffs(mT) - 1 : 0;
+    auto tp = [&](int i) { return (size_t)((i & (mT - 1)) * 32 + (i >> lmT)); };
     for (int i = c0; i < c1; ++i) {
         T l = T(0), D;
         if (i == 0) {
@@ -198,8 +204,10 @@ __global__ void __launch_bounds__(MAX_THREADS) k_factor(FactorArgs a)
             l = o / Dprev;
             D = dprime(i) - l * o;
         }
-        if constexpr (f64) { lf64[i] = l; iD64[i] = T(1) / D; }
-        else { lf32[i] = l; iD32[i] = T(1) / D; }
+        const T iD = T(1) / D;
+        if constexpr (f64) { lf64[i] = l; iD64[i] = iD; }
+        else { lf32[i] = l; iD32[i] = iD; }
+        if (lfT) { lfT[row + tp(i)] = l; iDT[row + tp(i)] = iD; }
         Dprev = D;
     }
     __syncthreads();
@@ -213,6 +221,7 @@ __global__ void __launch_bounds__(MAX_THREADS) k_factor(FactorArgs a)
         const T z = sb[i] * g;
         if constexpr (f64) a.zz[row + i] = z;
         else a.zz32[row + i] = z;
+        if (zT) zT[row + tp(i)] = z;
     }
     if (threadIdx.x == 0) {
         if constexpr (f64) { a.gam[j] = gam; a.ec[j] = ec; }

@@ -1,0 +1,586 @@
+// sw_warp.cuh -- the row work of the solver with one warp per latitude row.
+//
+// For grids whose rows outnumber the resident thread blocks, one block per
+// row leaves each SM with only one or two rows in flight, and every row phase
+// is a chain of dependent memory round trips (neighbour rows, coefficients,
+// zonal factors, store).  Here every warp of a block owns its own rows, so an
+// SM works on as many rows at once as it holds warps, and each row's loads
+// are issued as 16-byte vector loads over 4 consecutive points per lane.
+//
+// Layouts.  A lane works on 4 consecutive points per pass, 128 points per
+// warp pass (rows of a power of two of at least 128 points).  The zonal solve
+// of Eq. 13 gives each lane a chunk of m = nx/32 consecutive points: the
+// warp's row buffer holds point i at (i % m) * 33 + i / m, so both the chunk
+// walk of the solve and the coalesced passes are free of shared-memory bank
+// conflicts, and the zonal factors are stored transposed in global memory
+// (point i at (i % m) * 32 + i / m of its row) so that the chunk walk reads
+// them coalesced.  The arithmetic of each point is the one of the block
+// path (sw_rows.cuh, sw_solver.cu): the same expressions in the same order.
+#pragma once
+
+#include "sw_rows.cuh"
+
+namespace sw {
+
+// elements of one warp's row buffer
+__host__ __device__ inline int wbuf_len(int nx) { return (nx >> 5) * 33; }
+
+struct WRow {
+    int nx, m, lm;      // points per row, per lane chunk, log2 of the chunk
+};
+
+__device__ __forceinline__ WRow wrow(int nx)
+{
+    const int m = nx >> 5;
+    return WRow{nx, m, __ffs(m) - 1};
+}
+
+// buffer position of the first of 4 consecutive points i0 .. i0 + 3 (i0 a
+// multiple of 4); the others follow at strides of 33
+__device__ __forceinline__ int tpos4(const WRow &w, int i0) { return (i0 & (w.m - 1)) * 33 + (i0 >> w.lm); }
+__device__ __forceinline__ int tpos(const WRow &w, int i) { return (i & (w.m - 1)) * 33 + (i >> w.lm); }
+
+// ---------------------------------------------------------------------------
+// loads
+// ---------------------------------------------------------------------------
+// 6 consecutive values at longitudes a - 1 .. a + 4 (periodic) of a row of a
+// field written by other blocks during the launch (L2-coherent loads)
+__device__ __forceinline__ void cg6(const double *rowp, int a, int nx, double (&v)[6])
+{
+    const double2 q0 = __ldcg((const double2 *)(rowp + a)), q1 = __ldcg((const double2 *)(rowp + a) + 1);
+    v[1] = q0.x; v[2] = q0.y; v[3] = q1.x; v[4] = q1.y;
+    v[0] = __ldcg(rowp + (a == 0 ? nx - 1 : a - 1));
+    v[5] = __ldcg(rowp + (a + 4 == nx ? 0 : a + 4));
+}
+
+__device__ __forceinline__ void cg6(const float *rowp, int a, int nx, float (&v)[6])
+{
+    const float4 q = __ldcg((const float4 *)(rowp + a));
+    v[1] = q.x; v[2] = q.y; v[3] = q.z; v[4] = q.w;
+    v[0] = __ldcg(rowp + (a == 0 ? nx - 1 : a - 1));
+    v[5] = __ldcg(rowp + (a + 4 == nx ? 0 : a + 4));
+}
+
+// 16-bit values times the row scale (the dequantisation of stage3_q)
+template <class H>
+__device__ __forceinline__ void cg6h(const H *rowp, int a, int nx, float sc, float (&v)[6])
+{
+    const uint2 q = __ldcg((const uint2 *)(rowp + a));
+    H h[4];
+    memcpy(h, &q, sizeof(q));
+    v[1] = q_to_f(h[0]) * sc; v[2] = q_to_f(h[1]) * sc; v[3] = q_to_f(h[2]) * sc; v[4] = q_to_f(h[3]) * sc;
+    v[0] = q_to_f(__ldcg(rowp + (a == 0 ? nx - 1 : a - 1))) * sc;
+    v[5] = q_to_f(__ldcg(rowp + (a + 4 == nx ? 0 : a + 4))) * sc;
+}
+
+// one source row of a preconditioner field as the stencil sees it
+template <class Pol>
+struct QRow {
+    const typename Pol::q16 *h;     // 16-bit (or FP64) row
+    const float *f;                 // FP32 row (pole band, mixed policies)
+    float sc;                       // row scale of the 16-bit storage
+    int sh;                         // shift of a row beyond a pole
+    bool band;
+};
+
+template <class Pol>
+__device__ __forceinline__ QRow<Pol> qrow(const MemberDev<Pol> &M, const typename Pol::q16 *h, const float *f32,
+                                          const float *sc, int jj)
+{
+    int src, sh;
+    ghost_row(jj, M.nx, M.ny, src, sh);
+    QRow<Pol> q;
+    const size_t off = (size_t)src * M.nx;
+    q.h = h + off;
+    q.f = Pol::kMixed ? f32 + off : nullptr;
+    q.band = in_band(M, src);
+    q.sc = q_scale(M, sc, src);
+    q.sh = sh;
+    return q;
+}
+
+template <class Pol>
+__device__ __forceinline__ void q6(const QRow<Pol> &q, int i0, int nx, typename Pol::comp (&v)[6])
+{
+    int a = i0 + q.sh;
+    if (a >= nx) a -= nx;
+    if constexpr (!Pol::kMixed) cg6(q.h, a, nx, v);
+    else if (q.band) cg6(q.f, a, nx, v);
+    else cg6h(q.h, a, nx, q.sc, v);
+}
+
+// 4 values i0 .. i0 + 3 of the row's own preconditioner output (q_load)
+template <class Pol>
+__device__ __forceinline__ void q4own(const QRow<Pol> &q, int i0, typename Pol::comp (&v)[4])
+{
+    if constexpr (!Pol::kMixed) {
+        const double2 a = __ldcg((const double2 *)(q.h + i0)), b = __ldcg((const double2 *)(q.h + i0) + 1);
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    } else if (q.band) {
+        const float4 a = __ldcg((const float4 *)(q.f + i0));
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    } else {
+        const uint2 a = __ldcg((const uint2 *)(q.h + i0));
+        typename Pol::q16 h[4];
+        memcpy(h, &a, sizeof(a));
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = q_to_f(h[u]) * q.sc;
+    }
+}
+
+// face coefficients of points i0 .. i0 + 3 (read-only during the launch)
+template <class CT>
+struct Coef4 {
+    CT ax[5], cx[5], bx[5], ay[4], cy[4], by[4], ays[4], cys[4], bys[4], cc[4];
+};
+
+template <class CT>
+__device__ __forceinline__ void ldg4(const CT *p, CT (&v)[4])
+{
+    if constexpr (sizeof(CT) == 4) {
+        const float4 q = __ldg((const float4 *)p);
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    } else {
+        const double2 q0 = __ldg((const double2 *)p), q1 = __ldg((const double2 *)p + 1);
+        v[0] = q0.x; v[1] = q0.y; v[2] = q1.x; v[3] = q1.y;
+    }
+}
+
+template <class CT>
+__device__ __forceinline__ void coef4(const RowCoef<CT> &c, int i0, int nx, bool full, bool has_n, bool has_s,
+                                      Coef4<CT> &k)
+{
+    const int iw = i0 == 0 ? nx - 1 : i0 - 1;
+    CT q[4];
+    k.cx[0] = __ldg(c.cx + iw); k.bx[0] = __ldg(c.bx + iw);
+    ldg4(c.cx + i0, q); for (int u = 0; u < 4; ++u) k.cx[u + 1] = q[u];
+    ldg4(c.bx + i0, q); for (int u = 0; u < 4; ++u) k.bx[u + 1] = q[u];
+    if (full) {
+        k.ax[0] = __ldg(c.ax + iw);
+        ldg4(c.ax + i0, q); for (int u = 0; u < 4; ++u) k.ax[u + 1] = q[u];
+        ldg4(c.C + i0, k.cc);
+    } else {
+#pragma unroll
+        for (int u = 0; u < 5; ++u) k.ax[u] = CT(0);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) k.cc[u] = CT(0);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) { k.ay[u] = k.cy[u] = k.by[u] = k.ays[u] = k.cys[u] = k.bys[u] = CT(0); }
+    if (has_n) { ldg4(c.ay + i0, k.ay); ldg4(c.cy + i0, k.cy); ldg4(c.by + i0, k.by); }
+    if (has_s) { ldg4(c.ays + i0, k.ays); ldg4(c.cys + i0, k.cys); ldg4(c.bys + i0, k.bys); }
+}
+
+// the stencil of Eq. 10 (or P^M when the zonal a11 and C terms are zero) at
+// points i0 .. i0 + 3 from 6-point windows of the rows j (xc), j + 1 (xn) and
+// j - 1 (xs): the expressions of stencil_row4
+template <class T, class CT>
+__device__ __forceinline__ void apply4(const Coef4<CT> &k, const T (&xc)[6], const T (&xn)[6], const T (&xs)[6],
+                                       bool has_n, bool has_s, T (&y)[4])
+{
+    T F[5];
+#pragma unroll
+    for (int m = 0; m < 5; ++m)
+        F[m] = (T)k.cx[m] * (xn[m] + xn[m + 1] - xs[m] - xs[m + 1]) + (T)k.bx[m] * (xc[m] + xc[m + 1]) +
+               (T)k.ax[m] * (xc[m + 1] - xc[m]);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int q = u + 1;
+        T v = F[u + 1] - F[u];
+        if (has_n) v += (T)k.ay[u] * (xn[q] - xc[q]) + (T)k.cy[u] * (xc[q + 1] + xn[q + 1] - xc[q - 1] - xn[q - 1]) +
+                        (T)k.by[u] * (xc[q] + xn[q]);
+        if (has_s) v -= (T)k.ays[u] * (xc[q] - xs[q]) + (T)k.cys[u] * (xs[q + 1] + xc[q + 1] - xs[q - 1] - xc[q - 1]) +
+                        (T)k.bys[u] * (xs[q] + xc[q]);
+        y[u] = v - (T)k.cc[u] * xc[q];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// the cyclic zonal solve of Eq. 13 by one warp
+// ---------------------------------------------------------------------------
+// exclusive scan over the lanes of affine maps x -> a x + b, in lane order
+// (REV: reversed lane order); on return (a, b) composes the maps of the
+// earlier lanes (identity for the first)
+template <class T, bool REV>
+__device__ __forceinline__ void warp_affine_excl(T &a, T &b)
+{
+    const int lane = threadIdx.x & 31;
+    T ia = a, ib = b;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const T oa = REV ? __shfl_down_sync(0xffffffffu, ia, d) : __shfl_up_sync(0xffffffffu, ia, d);
+        const T ob = REV ? __shfl_down_sync(0xffffffffu, ib, d) : __shfl_up_sync(0xffffffffu, ib, d);
+        const bool ok = REV ? (lane + d < 32) : (lane >= d);
+        if (ok) { ib = ia * ob + ib; ia = ia * oa; }
+    }
+    T ea = REV ? __shfl_down_sync(0xffffffffu, ia, 1) : __shfl_up_sync(0xffffffffu, ia, 1);
+    T eb = REV ? __shfl_down_sync(0xffffffffu, ib, 1) : __shfl_up_sync(0xffffffffu, ib, 1);
+    if (REV ? lane == 31 : lane == 0) { ea = T(1); eb = T(0); }
+    a = ea;
+    b = eb;
+}
+
+// Solve the row's cyclic system T x = b in place in the warp's buffer: the
+// LDL^T factors of the non-cyclic part (multipliers lf with lf_0 = 0, inverse
+// pivots invD) and the Sherman-Morrison vector zz, as in trisolve_rm, but
+// read transposed (point t of lane l at t * 32 + l) and with each lane
+// walking its chunk of m points serially between two warp scans.
+template <class T, class F>
+__device__ __noinline__ void wtrisolve(T *wb, const WRow w, const F *__restrict__ lfT, const F *__restrict__ invDT,
+                                       const F *__restrict__ zzT, T gam, T ec)
+{
+    const int lane = threadIdx.x & 31, m = w.m;
+    T *col = wb + lane;
+    // forward elimination u_i = b_i - l_i u_{i-1}
+    T a = T(1), b = T(0);
+#pragma unroll 4
+    for (int t = 0; t < m; ++t) {
+        const T l = (T)__ldg(lfT + t * 32 + lane);
+        b = col[t * 33] - l * b;
+        a = -l * a;
+    }
+    warp_affine_excl<T, false>(a, b);
+    T u = b;
+#pragma unroll 4
+    for (int t = 0; t < m; ++t) {
+        const T l = (T)__ldg(lfT + t * 32 + lane);
+        u = col[t * 33] - l * u;
+        col[t * 33] = u * (T)__ldg(invDT + t * 32 + lane);
+    }
+    // back substitution y_i = v_i - l_{i+1} y_{i+1}
+    const T lfirst = (T)__ldg(lfT + lane);
+    const T lsh = __shfl_down_sync(0xffffffffu, lfirst, 1);
+    const T lnext = lane < 31 ? lsh : T(0);
+    a = T(1); b = T(0);
+#pragma unroll 4
+    for (int t = m - 1; t >= 0; --t) {
+        const T ln = t + 1 < m ? (T)__ldg(lfT + (t + 1) * 32 + lane) : lnext;
+        b = col[t * 33] - ln * b;
+        a = -ln * a;
+    }
+    warp_affine_excl<T, true>(a, b);
+    T y = b, ylast = T(0);
+#pragma unroll 4
+    for (int t = m - 1; t >= 0; --t) {
+        const T ln = t + 1 < m ? (T)__ldg(lfT + (t + 1) * 32 + lane) : lnext;
+        y = col[t * 33] - ln * y;
+        col[t * 33] = y;
+        if (t == m - 1) ylast = y;
+    }
+    // Sherman-Morrison correction with y_0 (lane 0, t = 0) and y_{n-1}
+    // (lane 31, t = m - 1)
+    const T y0 = __shfl_sync(0xffffffffu, y, 0);
+    const T yn = __shfl_sync(0xffffffffu, ylast, 31);
+    const T s = gam * y0 + ec * yn;
+#pragma unroll 4
+    for (int t = 0; t < m; ++t) col[t * 33] -= (T)__ldg(zzT + t * 32 + lane) * s;
+}
+
+// store row j of a preconditioner field from the warp's buffer (q_store_row:
+// FP64; FP32 on the pole band; else 16-bit with a power-of-two row scale so
+// that the stored magnitudes are at most 1)
+template <class Pol>
+__device__ void wq_store_row(const MemberDev<Pol> &M, typename Pol::q16 *h, float *f32, float *sc, int j,
+                             const typename Pol::comp *wb, const WRow w)
+{
+    typedef typename Pol::q16 qt;
+    const int lane = threadIdx.x & 31, nx = w.nx;
+    const size_t row = (size_t)j * nx;
+    if constexpr (!Pol::kMixed) {
+        for (int i = 2 * lane; i < nx; i += 64)
+            *(double2 *)(h + row + i) = make_double2(wb[tpos(w, i)], wb[tpos(w, i + 1)]);
+    } else {
+        if (in_band(M, j)) {
+            for (int i = 2 * lane; i < nx; i += 64)
+                *(float2 *)(f32 + row + i) = make_float2(wb[tpos(w, i)], wb[tpos(w, i + 1)]);
+        } else {
+            float mx = 0.f;
+            for (int t = 0; t < w.m; ++t) mx = fmaxf(mx, fabsf(wb[t * 33 + lane]));
+            mx = warp_max(mx);
+            float s = 1.f;
+            if (mx > 0.f && mx <= 3.0e38f) { int e; frexpf(mx, &e); s = ldexpf(1.f, e); }
+            else if (!(mx <= 3.0e38f)) s = mx;       // NaN / Inf: propagate
+            const float inv = 1.f / s;                // exact: s is a power of two
+            for (int i = 2 * lane; i < nx; i += 64) {
+                qt q[2] = {f_to_q<qt>(wb[tpos(w, i)] * inv), f_to_q<qt>(wb[tpos(w, i + 1)] * inv)};
+                unsigned u;
+                memcpy(&u, q, sizeof(u));
+                *(unsigned *)(h + row + i) = u;
+            }
+            if (lane == 0) sc[j] = s;
+        }
+    }
+}
+
+// the zonal solve (option 3) and the store of the first preconditioner stage
+// of row j, whose input the warp's buffer holds (stage0_finish)
+template <class Pol>
+__device__ void wstage0_finish(const MemberDev<Pol> &M, const RowView<Pol> &v, int j, typename Pol::comp *wb,
+                               const WRow w)
+{
+    typedef typename Pol::comp comp;
+    const size_t row = (size_t)j * M.nx;
+    __syncwarp();
+    SW_TRACE(211);
+    if (M.pc >= 3) wtrisolve<comp, typename Pol::fac>(wb, w, M.lfT + row, M.invDT + row, M.zzT + row, (comp)v.gam, (comp)v.ec);
+    __syncwarp();
+    SW_TRACE(212);
+    if (M.nstages == 1) wq_store_row(M, M.e, M.e32, M.e_s, j, wb, w);
+    else wq_store_row(M, M.qa, M.qa32, M.qa_s, j, wb, w);
+    __syncwarp();
+    SW_TRACE(213);
+}
+
+// ---------------------------------------------------------------------------
+// phases on one row j (one warp); the thread adds its share of the phase's
+// inner products to part (phase_true, phase_ub, precond_stage, phase_le)
+// ---------------------------------------------------------------------------
+template <class Pol, int NP>
+__device__ void wphase_true(const MemberDev<Pol> &M, const RowView<Pol> &v, typename Pol::comp eta, int j,
+                            typename Pol::comp *wb, const WRow w, typename Acc<Pol>::type (&part)[NP])
+{
+    typedef typename Pol::comp comp;
+    const int nx = M.nx, ny = M.ny, lane = threadIdx.x & 31;
+    const size_t row = (size_t)j * nx, rs = j > 0 ? row - nx : row;
+    const RowCoef<double> c = {M.ax + row, M.cx + row, M.bx + row, M.ay + row, M.cy + row, M.by + row,
+                               M.ay + rs, M.cy + rs, M.by + rs, M.C + row};
+    int srcS, shS, srcN, shN;
+    ghost_row(j - 1, nx, ny, srcS, shS);
+    ghost_row(j + 1, nx, ny, srcN, shN);
+    const double *pX = M.phi + row, *pN = M.phi + (size_t)srcN * nx, *pS = M.phi + (size_t)srcS * nx;
+    const bool has_n = j < ny - 1, has_s = j > 0;
+    double rr = 0.0, RR = 0.0;
+    for (int i0 = 4 * lane; i0 < nx; i0 += 128) {
+        double xc[6], xn[6], xs[6];
+        cg6(pX, i0, nx, xc);
+        int a = i0 + shN; if (a >= nx) a -= nx;
+        cg6(pN, a, nx, xn);
+        a = i0 + shS; if (a >= nx) a -= nx;
+        cg6(pS, a, nx, xs);
+        Coef4<double> k;
+        coef4(c, i0, nx, true, has_n, has_s, k);
+        double Rv[4];
+        ldg4(M.R + row + i0, Rv);
+        double lphi[4];
+        apply4(k, xc, xn, xs, has_n, has_s, lphi);
+        const int p0 = tpos4(w, i0);
+        typename Pol::res r4[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const double rv = lphi[u] - Rv[u];
+            r4[u] = (typename Pol::res)rv;
+            rr += rv * rv;
+            RR += Rv[u] * Rv[u];
+            wb[p0 + 33 * u] = stage0_input(M, v, eta, (comp)r4[u], i0 + u);
+        }
+        stv4(v.r + i0, r4);
+    }
+    part[0] += (typename Acc<Pol>::type)rr;
+    part[1] += (typename Acc<Pol>::type)RR;
+    wstage0_finish(M, v, j, wb, w);
+}
+
+template <class Pol, int KM>
+__device__ void wphase_ub(const MemberDev<Pol> &M, const MemberCtl &c, const RowView<Pol> &v,
+                          typename Pol::comp eta, int j, typename Pol::comp *wb, const WRow w,
+                          typename Acc<Pol>::type (&part)[2 + 2 * KM])
+{
+    typedef typename Pol::comp comp;
+    typedef typename Pol::vec vec;
+    typedef typename Acc<Pol>::type acc_t;
+    const int nx = M.nx, lane = threadIdx.x & 31;
+    const size_t row = (size_t)j * nx;
+    const int nd = c.nu + 1;                      // directions before the new one
+    vec *pn = v.pb + (size_t)phys_slot(c, M.k, nd) * v.vstride;
+    vec *Lpn = v.Lpb + (size_t)phys_slot(c, M.k, nd) * v.vstride;
+    const vec *pl[KM], *Lpl[KM];
+    comp al[KM];
+#pragma unroll
+    for (int l = 0; l < KM; ++l) {
+        const size_t off = (size_t)phys_slot(c, M.k, l < nd ? l : 0) * v.vstride;
+        pl[l] = v.pb + off;
+        Lpl[l] = v.Lpb + off;
+        al[l] = l < nd ? (comp)c.alpha[l] : (comp)0;
+    }
+    const QRow<Pol> eq = qrow(M, M.e, M.e32, M.e_s, j);
+    const double beta = c.beta;
+    const comp beta_c = (comp)beta;
+    double *ph = M.phi + row;
+    for (int i0 = 4 * lane; i0 < nx; i0 += 128) {
+        comp ev[4];
+        vec le4[4], pv4[KM][4], lp4[KM][4];
+        typename Pol::res r4[4];
+        double ph4[4];
+        q4own(eq, i0, ev);
+        ldv4(v.Le + i0, le4);
+        ldv4(v.r + i0, r4);
+        ldv4(ph + i0, ph4);
+#pragma unroll
+        for (int l = 0; l < KM; ++l) {
+            if (l < nd) {
+                ldv4(pl[l] + i0, pv4[l]);
+                ldv4(Lpl[l] + i0, lp4[l]);
+            }
+        }
+        vec ps4[4], ls4[4];
+        typename Pol::res rs4[4];
+        double phn[4];
+        const int p0 = tpos4(w, i0);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            comp pv = ev[u], lw = (comp)le4[u];
+#pragma unroll
+            for (int l = 0; l < KM; ++l) {
+                if (l < nd) {
+                    pv += al[l] * (comp)pv4[l][u];
+                    lw += al[l] * (comp)lp4[l][u];
+                }
+            }
+            ps4[u] = (vec)pv;
+            ls4[u] = (vec)lw;
+            phn[u] = ph4[u] + beta * (double)ps4[u];
+            if constexpr (Pol::kMixed) rs4[u] = (typename Pol::res)((comp)r4[u] + beta_c * ls4[u]);
+            else rs4[u] = (comp)r4[u] + beta * ls4[u];
+            const acc_t ra = (acc_t)rs4[u], la = (acc_t)ls4[u];
+            part[0] += ra * ra;
+            part[1] += la * la;
+#pragma unroll
+            for (int l = 0; l < KM; ++l)
+                if (l < nd) part[2 + l] += la * (acc_t)lp4[l][u];
+            wb[p0 + 33 * u] = stage0_input(M, v, eta, (comp)rs4[u], i0 + u);
+        }
+        stv4(pn + i0, ps4);
+        stv4(Lpn + i0, ls4);
+        stv4(ph + i0, phn);
+        stv4(v.r + i0, rs4);
+    }
+    wstage0_finish(M, v, j, wb, w);
+}
+
+// Richardson stage mu >= 1 (precond_stage): reads q_mu on rows j - 1 .. j + 1,
+// writes q_{mu+1} (the last stage writes e)
+template <class Pol>
+__device__ void wprecond_stage(const MemberDev<Pol> &M, const RowView<Pol> &v, typename Pol::comp eta, int mu,
+                               int j, typename Pol::comp *wb, const WRow w)
+{
+    typedef typename Pol::comp comp;
+    typedef typename Pol::coef CT;
+    const int nx = M.nx, ny = M.ny, lane = threadIdx.x & 31;
+    const bool last = (mu == M.nstages - 1);
+    const typename Pol::q16 *ih = (mu & 1) ? M.qa : M.qb;
+    const float *if32 = (mu & 1) ? M.qa32 : M.qb32;
+    const float *is = (mu & 1) ? M.qa_s : M.qb_s;
+    typename Pol::q16 *oh = last ? M.e : ((mu & 1) ? M.qb : M.qa);
+    float *of32 = last ? M.e32 : ((mu & 1) ? M.qb32 : M.qa32);
+    float *os = last ? M.e_s : ((mu & 1) ? M.qb_s : M.qa_s);
+    const QRow<Pol> qS = qrow(M, ih, if32, is, j - 1), qX = qrow(M, ih, if32, is, j), qN = qrow(M, ih, if32, is, j + 1);
+    const bool opt3 = (M.pc >= 3), has_n = j < ny - 1, has_s = j > 0;
+    const RowCoef<CT> c = coef_of(v);
+    for (int i0 = 4 * lane; i0 < nx; i0 += 128) {
+        comp xc[6], xn[6], xs[6];
+        q6(qX, i0, nx, xc);
+        q6(qN, i0, nx, xn);
+        q6(qS, i0, nx, xs);
+        Coef4<CT> k;
+        coef4(c, i0, nx, !opt3, has_n, has_s, k);
+        comp rv[4], dg[4] = {comp(1), comp(1), comp(1), comp(1)};
+        ldv4(v.r + i0, rv);
+        if (!opt3) {
+            CT d4[4];
+            ldg4(v.diag + i0, d4);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) dg[u] = (comp)d4[u];
+        }
+        comp y[4];
+        apply4(k, xc, xn, xs, has_n, has_s, y);
+        const int p0 = tpos4(w, i0);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const comp xv = xc[u + 1];
+            wb[p0 + 33 * u] = opt3 ? xv + eta * (y[u] - rv[u]) : xv + (comp)M.omega * (rv[u] - y[u]) / dg[u];
+        }
+    }
+    __syncwarp();
+    SW_TRACE(311);
+    const size_t row = (size_t)j * nx;
+    if (opt3) wtrisolve<comp, typename Pol::fac>(wb, w, M.lfT + row, M.invDT + row, M.zzT + row, (comp)v.gam, (comp)v.ec);
+    __syncwarp();
+    SW_TRACE(312);
+    wq_store_row(M, oh, of32, os, j, wb, w);
+    __syncwarp();
+    SW_TRACE(313);
+}
+
+// L(e) of row j into the row's L e and the inner products <Le,Le>, <r,Le>,
+// <Le,Lp_l>, <r,Lp_l> (phase_le)
+template <class Pol, int KM>
+__device__ void wphase_le(const MemberDev<Pol> &M, const MemberCtl &c, const RowView<Pol> &v, int j, const WRow w,
+                          typename Acc<Pol>::type (&part)[2 + 2 * KM])
+{
+    typedef typename Pol::comp comp;
+    typedef typename Pol::vec vec;
+    typedef typename Pol::coef CT;
+    typedef typename Acc<Pol>::type acc_t;
+    const int nx = M.nx, ny = M.ny, lane = threadIdx.x & 31;
+    const int nd = c.nu + 1;
+    const QRow<Pol> qS = qrow(M, M.e, M.e32, M.e_s, j - 1), qX = qrow(M, M.e, M.e32, M.e_s, j),
+                    qN = qrow(M, M.e, M.e32, M.e_s, j + 1);
+    const bool has_n = j < ny - 1, has_s = j > 0;
+    const RowCoef<CT> cf = coef_of(v);
+    const vec *Lpl[KM];
+#pragma unroll
+    for (int l = 0; l < KM; ++l) Lpl[l] = v.Lpb + (size_t)phys_slot(c, M.k, l < nd ? l : 0) * v.vstride;
+    for (int i0 = 4 * lane; i0 < nx; i0 += 128) {
+        comp xc[6], xn[6], xs[6];
+        q6(qX, i0, nx, xc);
+        q6(qN, i0, nx, xn);
+        q6(qS, i0, nx, xs);
+        Coef4<CT> k;
+        coef4(cf, i0, nx, true, has_n, has_s, k);
+        typename Pol::res r4[4];
+        vec lp4[KM][4];
+        ldv4(v.r + i0, r4);
+#pragma unroll
+        for (int l = 0; l < KM; ++l)
+            if (l < nd) ldv4(Lpl[l] + i0, lp4[l]);
+        comp y[4];
+        apply4(k, xc, xn, xs, has_n, has_s, y);
+        vec le4[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) le4[u] = (vec)y[u];
+        stv4(v.Le + i0, le4);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const acc_t la = (acc_t)le4[u], rv = (acc_t)r4[u];
+            part[0] += la * la;
+            part[1] += rv * la;
+#pragma unroll
+            for (int l = 0; l < KM; ++l) {
+                if (l < nd) {
+                    part[2 + l] += la * (acc_t)lp4[l][u];
+                    part[2 + KM + l] += rv * (acc_t)lp4[l][u];
+                }
+            }
+        }
+    }
+    SW_TRACE(111);
+}
+
+// the first stage of option 3 from the stored r (phase_prec0)
+template <class Pol>
+__device__ void wphase_prec0(const MemberDev<Pol> &M, const RowView<Pol> &v, typename Pol::comp eta, int j,
+                             typename Pol::comp *wb, const WRow w)
+{
+    typedef typename Pol::comp comp;
+    const int lane = threadIdx.x & 31;
+    for (int i0 = 4 * lane; i0 < M.nx; i0 += 128) {
+        typename Pol::res r4[4];
+        ldv4(v.r + i0, r4);
+        const int p0 = tpos4(w, i0);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) wb[p0 + 33 * u] = stage0_input(M, v, eta, (comp)r4[u], i0 + u);
+    }
+    wstage0_finish(M, v, j, wb, w);
+}
+
+} // namespace sw

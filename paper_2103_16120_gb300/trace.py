@@ -12,9 +12,12 @@ Tags: 10 + phase at the start of a phase (phases: 0 true residual, 1 update,
 scalars, 36 after the state transition, 34 after the block has synchronised;
 inside the rows 101/102 (L(e): staging, stencil), 201 (update
 loop), 301/302/303 (stage: staging, stencil, zonal solve), 401/402 (first
-stage: zonal solve, store).
+stage: zonal solve, store); with one warp per row (warp 0 of the block) 111
+(after L(e) and its inner products), 211/212/213 (first stage: before the
+zonal solve, after it, after the store), 311/312/313 (stage: after the
+stencil, the zonal solve, the store).
 
-    python -m paper_2103_16120_gb300.trace NX NY PREC [BLOCK]
+    python -m paper_2103_16120_gb300.trace NX NY PREC [BLOCK [ROW_MODE]]
 """
 from __future__ import annotations
 
@@ -26,7 +29,8 @@ import sys
 import numpy as np
 
 
-def timeline(nx: int, ny: int, prec: int, block: int = 0, seed: int = 1000, tol: float = 1e-8) -> dict:
+def timeline(nx: int, ny: int, prec: int, block: int = 0, seed: int = 1000, tol: float = 1e-8,
+             row_mode: int = 0) -> dict:
     import torch
 
     from . import _lib as L
@@ -43,7 +47,7 @@ def timeline(nx: int, ny: int, prec: int, block: int = 0, seed: int = 1000, tol:
     g = sw.sw_grid_create(nx, ny)
     sw.sw_elliptic_set_coeffs(g, *[torch.as_tensor(P[k], device="cuda") for k in sw.COEFF_KEYS])
     R = torch.as_tensor(P["R"], device="cuda")
-    o = sw.sw_solve_opts_default(prec=prec, tol=tol, max_iters=5000)
+    o = sw.sw_solve_opts_default(prec=prec, tol=tol, max_iters=5000, row_mode=row_mode)
     ms = []
     for _ in range(3):
         phi = torch.zeros_like(R)
@@ -76,4 +80,4 @@ if __name__ == "__main__":
     args = [int(a) for a in sys.argv[1:]]
     if len(args) < 3:
         sys.exit(__doc__)
-    print(json.dumps(timeline(*args[:4])))
+    print(json.dumps(timeline(*args[:4], row_mode=args[4] if len(args) > 4 else 0)))

@@ -87,12 +87,14 @@ def test_sequence_512x256_warm_start():
     assert np.linalg.norm(x - ref) <= 1e-6 * np.linalg.norm(ref)
 
 
+@pytest.mark.parametrize("row_mode", [1, 2])
 @pytest.mark.parametrize("nx,ny,iters", [(1024, 512, 6), (2048, 1024, 5)])
-def test_multirow_blocks_fp64_fixed_iterations(nx, ny, iters):
-    """Grids whose rows outnumber the resident blocks: every block owns several
-    rows, reads them through global memory and runs the instantiation built for
-    two resident blocks per SM.  FP64 iterates after a fixed number of
-    iterations against the oracle's.
+def test_multirow_blocks_fp64_fixed_iterations(nx, ny, iters, row_mode):
+    """Grids whose rows outnumber the resident blocks, in both row modes:
+    thread blocks that each own several rows (row_mode 1, the instantiation
+    built for two resident blocks per SM), and one warp per row (row_mode 2,
+    the automatic choice at these widths).  FP64 iterates after a fixed number
+    of iterations against the oracle's.
 
     The bar comes from the conditioning.  One rounding of R (relative 1e-16)
     moves the oracle's own iterates by s: 6e-16 at 512 x 256, 4e-14 at
@@ -103,7 +105,7 @@ def test_multirow_blocks_fp64_fixed_iterations(nx, ny, iters):
     g = grid_for(P)
     R = torch.as_tensor(P["R"], device="cuda")
     phi = torch.zeros_like(R)
-    o = sw.sw_solve_opts_default(k=4, tol=0.0, max_iters=iters)
+    o = sw.sw_solve_opts_default(k=4, tol=0.0, max_iters=iters, row_mode=row_mode)
     st = sw.sw_gcr_solve(g, o, R, phi)
     assert st.iterations == iters and st.status == sw.SW_ERR_NOT_CONVERGED
     prob = O.Problem(P)
