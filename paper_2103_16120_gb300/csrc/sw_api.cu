@@ -512,7 +512,7 @@ extern "C" sw_status sw_precond_apply(sw_grid g, const sw_solve_opts *o, const v
 // linearly with the resolution) and cycle over several rows each, with
 // everything in global memory.
 struct Plan {
-    int grid = 0, cc = 0, cs = 0, threads = 0, minb = 1, warp = 0;
+    int grid = 0, cc = 0, cs = 0, threads = 0, minb = 1, warp = 0, stage = 0;
     size_t smem = 0;
     std::vector<int> nb;
 };
@@ -545,10 +545,17 @@ static sw_status plan_launch(int n, const sw_grid *grids, const sw_solve_opts *o
         // 128 points: one warp per row (every SM works on as many rows at once
         // as it holds warps), on every SM
         P.threads = MAX_THREADS;
-        P.smem = gcr_warp_smem_bytes(o->prec, max_nx, P.threads);
         P.cc = P.cs = 0;
+        // the rows' zonal factors staged in shared memory where they fit
         int bps = 0, bps2 = 0;
+        P.stage = 1;
+        P.smem = gcr_warp_smem_bytes(o->prec, max_nx, P.threads, 1);
         CK(gcr_occupancy(o->prec, o->k, 1, 1, P.threads, P.smem, &bps));
+        if (bps < 1) {
+            P.stage = 0;
+            P.smem = gcr_warp_smem_bytes(o->prec, max_nx, P.threads, 0);
+            CK(gcr_occupancy(o->prec, o->k, 1, 1, P.threads, P.smem, &bps));
+        }
         CK(gcr_occupancy(o->prec, o->k, 2, 1, P.threads, P.smem, &bps2));
         const int warps = P.threads / 32;
         const int need = (grids[0]->ny + warps - 1) / warps;   // blocks that give every row its own warp
@@ -609,6 +616,7 @@ static void fill_desc(EnsDesc &D, int n, const sw_grid *grids, const Plan &P, sw
     D.cache_const = P.cc;
     D.cache_state = P.cs;
     D.warp_rows = P.warp;
+    D.warp_stage = P.stage;
     D.cta_begin[0] = 0;
     for (int m = 0; m < n; ++m) {
         D.cta_begin[m + 1] = D.cta_begin[m] + P.nb[m];
@@ -677,6 +685,7 @@ static sw_status solve_one_async(sw_grid g, const sw_solve_opts *o, const double
     a.cache_const = P.cc;
     a.cache_state = P.cs;
     a.warp_rows = P.warp;
+    a.warp_stage = P.stage;
     CK(launch_init_one(a, s));
     CK(launch_gcr(o->prec, o->k, P.minb, P.warp, g->desc, P.grid, max_nx, P.threads, P.smem, s));
     return SW_OK;

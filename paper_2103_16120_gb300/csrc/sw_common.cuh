@@ -161,14 +161,15 @@ struct InitOneArgs {
     SolverBlock *blk;
     struct EnsDesc *desc;
     sw_solve_stats *stats;
-    int grid, nb0, cache_const, cache_state, warp_rows;
+    int grid, nb0, cache_const, cache_state, warp_rows, warp_stage;
 };
 
 // members of one persistent launch and their block ranges
 struct EnsDesc {
     int n, grid;
     int cache_const, cache_state;   // row constants / owner-only vectors in shared memory
-    int warp_rows, pad_;            // one warp per latitude row (sw_warp.cuh) instead of one block
+    int warp_rows;                  // one warp per latitude row (sw_warp.cuh) instead of one block
+    int warp_stage;                 // warp mode: rows' zonal factors staged in shared memory
     sw_solve_stats *stats;          // device, n entries, or null: each member's stats at the end
     int cta_begin[MAX_MEMBERS + 1];
     SolverBlock *blk[MAX_MEMBERS];

@@ -654,8 +654,31 @@ __global__ void __launch_bounds__(MAX_THREADS, MINB) k_gcr(const EnsDesc *__rest
     constexpr bool wmode = WARP;          // one warp per row (D->warp_rows)
     const WRow wr = wrow(nx);
     double *scratch;
-    if constexpr (wmode) scratch = (double *)(ws + al16((size_t)nwarps() * wbuf_len(nx) * sizeof(comp)));
-    else scratch = (double *)(ws + red_offset<Pol>(nx));
+    typedef typename Pol::fac fac_t;
+    WFac<fac_t> wf = {nullptr, nullptr, 0u, 0u, &B->g.abort};
+    comp *wb = nullptr;
+    if constexpr (wmode) {
+        // per warp: row buffer, staged factor rows, mbarrier (warp_slot_bytes)
+        const bool stage = D->warp_stage != 0;
+        const size_t slot = warp_slot_bytes<Pol>(nx, stage);
+        unsigned char *mine = ws + (size_t)(threadIdx.x >> 5) * slot;
+        wb = (comp *)mine;
+        if (stage) {
+            const size_t wbuf = al16((size_t)wbuf_len(nx) * sizeof(comp));
+            wf.lf = (fac_t *)(mine + wbuf);
+            wf.iD = wf.lf + nx;
+            unsigned long long *bar = (unsigned long long *)(mine + wbuf + al16(2 * (size_t)nx * sizeof(fac_t)));
+            wf.bar = smem_u32(bar);
+            if ((threadIdx.x & 31) == 0) {
+                asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(wf.bar) : "memory");
+                asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            }
+            __syncwarp();
+        }
+        scratch = (double *)(ws + (size_t)nwarps() * slot);
+    } else {
+        scratch = (double *)(ws + red_offset<Pol>(nx));
+    }
     unsigned char *cslot = dsm + work_bytes<Pol>(max_nx);
     unsigned char *sslot = cslot + (D->cache_const ? const_bytes<Pol>(max_nx) : 0);
     // this block's rows: j = local + t * nb; the first one may be cached
@@ -682,16 +705,15 @@ __global__ void __launch_bounds__(MAX_THREADS, MINB) k_gcr(const EnsDesc *__rest
             // one warp per row: warp w of the member's block `local` owns rows
             // w * nb + local + t * (nb * warps)
             const int wi = threadIdx.x >> 5, NW = nb * nwarps();
-            comp *wb = (comp *)ws + (size_t)wi * wbuf_len(nx);
             for (int j = wi * nb + local; j < ny; j += NW) {
                 RowView<Pol> v;
                 view_const_global(M, j, v);
                 view_state_global(M, j, v);
                 switch (s_c.phase) {
-                case PH_TRUE: wphase_true<Pol, NP>(M, v, eta, j, wb, wr, part); break;
-                case PH_UB: wphase_ub<Pol, KM>(M, s_c, v, eta, j, wb, wr, part); break;
-                case PH_PREC: wprecond_stage<Pol>(M, v, eta, s_c.stage, j, wb, wr); break;
-                case PH_PREC0: wphase_prec0<Pol>(M, v, eta, j, wb, wr); break;
+                case PH_TRUE: wphase_true<Pol, NP>(M, v, eta, j, wb, wr, wf, part); break;
+                case PH_UB: wphase_ub<Pol, KM>(M, s_c, v, eta, j, wb, wr, wf, part); break;
+                case PH_PREC: wprecond_stage<Pol>(M, v, eta, s_c.stage, j, wb, wr, wf); break;
+                case PH_PREC0: wphase_prec0<Pol>(M, v, eta, j, wb, wr, wf); break;
                 case PH_LE: wphase_le<Pol, KM>(M, s_c, v, j, wr, part); break;
                 case PH_ZERO:
                     for (int i = threadIdx.x & 31; i < nx; i += 32) M.phi[(size_t)j * nx + i] = 0.0;

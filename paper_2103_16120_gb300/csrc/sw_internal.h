@@ -54,7 +54,7 @@ cudaError_t launch_faces(const FaceArgs &a, int threads, cudaStream_t s);
 cudaError_t launch_factor(const FactorArgs &a, bool fp64, int threads, cudaStream_t s);
 size_t gcr_smem_bytes(int prec, int max_nx, int k, int cache_const, int cache_state);
 // shared memory of the warp-per-row mode (0 when nx does not allow it)
-size_t gcr_warp_smem_bytes(int prec, int nx, int threads);
+size_t gcr_warp_smem_bytes(int prec, int nx, int threads, int stage);
 cudaError_t gcr_occupancy(int prec, int k, int minb, int warp, int threads, size_t smem, int *blocks_per_sm);
 cudaError_t launch_gcr(int prec, int k, int minb, int warp, const EnsDesc *Ddev, int grid, int max_nx, int threads,
                        size_t smem, cudaStream_t s);

@@ -189,15 +189,15 @@ static size_t smem_t(int max_nx, int k, int cache_const, int cache_state)
 }
 
 template <class Pol>
-static size_t warp_smem_t(int nx, int threads)
+static size_t warp_smem_t(int nx, int threads, bool stage)
 {
-    return al16((size_t)(threads / 32) * wbuf_len(nx) * sizeof(typename Pol::comp)) + al16(RED_WORDS * sizeof(double));
+    return (size_t)(threads / 32) * warp_slot_bytes<Pol>(nx, stage) + al16(RED_WORDS * sizeof(double));
 }
 
-size_t gcr_warp_smem_bytes(int prec, int nx, int threads)
+size_t gcr_warp_smem_bytes(int prec, int nx, int threads, int stage)
 {
     if (!warp_rows_ok(nx)) return 0;
-    return prec == 0 ? warp_smem_t<PolFP64>(nx, threads) : warp_smem_t<PolF16>(nx, threads);
+    return prec == 0 ? warp_smem_t<PolFP64>(nx, threads, stage) : warp_smem_t<PolF16>(nx, threads, stage);
 }
 
 size_t gcr_smem_bytes(int prec, int max_nx, int k, int cache_const, int cache_state)
@@ -357,6 +357,7 @@ __global__ void k_init_one(const __grid_constant__ InitOneArgs a)
         D->cache_const = a.cache_const;
         D->cache_state = a.cache_state;
         D->warp_rows = a.warp_rows;
+        D->warp_stage = a.warp_stage;
         D->stats = a.stats;
         D->cta_begin[0] = 0;
         D->cta_begin[1] = a.nb0;

@@ -196,6 +196,95 @@ __device__ __forceinline__ void apply4(const Coef4<CT> &k, const T (&xc)[6], con
 }
 
 // ---------------------------------------------------------------------------
+// staging of a row's zonal factors into shared memory
+// ---------------------------------------------------------------------------
+// The serial chunk walks of the zonal solve read the row's multipliers and
+// inverse pivots several times.  One lane of the warp copies both transposed
+// rows into the warp's shared memory with two bulk asynchronous copies
+// (cp.async.bulk, completion counted on the warp's mbarrier) when the row's
+// phase begins, so that the copy overlaps the stencil or update pass and the
+// walks then read shared memory.
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long wtimer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// longest wait for a staging copy: a copy of two rows takes microseconds
+constexpr unsigned long long STAGE_WAIT_NS = 200000000ull;
+
+template <class F>
+struct WFac {
+    F *lf, *iD;            // the row's transposed lf and invD in shared memory (null: read from global)
+    unsigned bar;          // shared address of the warp's mbarrier
+    unsigned parity;       // phase parity of the next wait
+    int *abort;            // the member's abort flag, set when a wait runs out
+};
+
+// lane 0 starts the copy of one or two rows (src1 optional) into the warp's
+// buffers dst0, dst1
+template <class F>
+__device__ __forceinline__ void wfac_copy(const WFac<F> &f, F *dst0, const F *src0, F *dst1, const F *src1, int nx)
+{
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) {
+        const unsigned bytes = (unsigned)(nx * sizeof(F));
+        // the warp's earlier reads of the buffers come before the async writes
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(f.bar), "r"(src1 ? 2 * bytes : bytes)
+                     : "memory");
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                     ::"r"(smem_u32(dst0)), "l"(src0), "r"(bytes), "r"(f.bar) : "memory");
+        if (src1)
+            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                         ::"r"(smem_u32(dst1)), "l"(src1), "r"(bytes), "r"(f.bar) : "memory");
+    }
+}
+
+// the row's multipliers and inverse pivots, when its phase begins
+template <class F>
+__device__ __forceinline__ void wfac_issue(const WFac<F> &f, const F *lfT, const F *iDT, int nx)
+{
+    if (f.lf) wfac_copy(f, f.lf, lfT, f.iD, iDT, nx);
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity)
+{
+    unsigned long long t0 = 0;
+    for (unsigned n = 0;; ++n) {
+        unsigned done;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     " selp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(done)
+                     : "r"(bar), "r"(parity)
+                     : "memory");
+        if (done) return true;
+        if ((n & 63) == 0) {
+            const unsigned long long t = wtimer();
+            if (n == 0) t0 = t;
+            else if (t - t0 > STAGE_WAIT_NS) return false;
+        }
+    }
+}
+
+// every lane waits for the staged rows; a wait that runs out sets the abort
+// flag (the solve then ends with SW_ERR_TIMEOUT) and waits once more, again
+// bounded, for the copies in flight
+template <class F>
+__device__ __forceinline__ void wfac_wait(WFac<F> &f)
+{
+    if (!f.lf) return;
+    if (!mbar_wait_bounded(f.bar, f.parity)) {
+        if ((threadIdx.x & 31) == 0) atomicExch(f.abort, 1);
+        mbar_wait_bounded(f.bar, f.parity);
+    }
+    f.parity ^= 1u;
+}
+
+// ---------------------------------------------------------------------------
 // the cyclic zonal solve of Eq. 13 by one warp
 // ---------------------------------------------------------------------------
 // exclusive scan over the lanes of affine maps x -> a x + b, in lane order
@@ -223,57 +312,70 @@ __device__ __forceinline__ void warp_affine_excl(T &a, T &b)
 // Solve the row's cyclic system T x = b in place in the warp's buffer: the
 // LDL^T factors of the non-cyclic part (multipliers lf with lf_0 = 0, inverse
 // pivots invD) and the Sherman-Morrison vector zz, as in trisolve_rm, but
-// read transposed (point t of lane l at t * 32 + l) and with each lane
-// walking its chunk of m points serially between two warp scans.
+// transposed (point t of lane l at t * 32 + l, in shared memory when staged)
+// and with each lane walking its chunk of m points serially between two warp
+// scans.
 template <class T, class F>
-__device__ __noinline__ void wtrisolve(T *wb, const WRow w, const F *__restrict__ lfT, const F *__restrict__ invDT,
-                                       const F *__restrict__ zzT, T gam, T ec)
+__device__ __noinline__ void wtrisolve(T *wb, const WRow w, const F *lfT, const F *invDT, const F *__restrict__ zzT,
+                                       T gam, T ec, WFac<F> &f)
 {
     const int lane = threadIdx.x & 31, m = w.m;
     T *col = wb + lane;
+    const F *lc = lfT + lane, *dc = invDT + lane;
     // forward elimination u_i = b_i - l_i u_{i-1}
     T a = T(1), b = T(0);
-#pragma unroll 4
+#pragma unroll 8
     for (int t = 0; t < m; ++t) {
-        const T l = (T)__ldg(lfT + t * 32 + lane);
+        const T l = (T)lc[t * 32];
         b = col[t * 33] - l * b;
         a = -l * a;
     }
+    SW_TRACE(221);
     warp_affine_excl<T, false>(a, b);
     T u = b;
-#pragma unroll 4
+#pragma unroll 8
     for (int t = 0; t < m; ++t) {
-        const T l = (T)__ldg(lfT + t * 32 + lane);
+        const T l = (T)lc[t * 32];
         u = col[t * 33] - l * u;
-        col[t * 33] = u * (T)__ldg(invDT + t * 32 + lane);
+        col[t * 33] = u * (T)dc[t * 32];
+    }
+    SW_TRACE(222);
+    // staged rows: the Sherman-Morrison vector goes into the inverse pivots'
+    // buffer, which the walks no longer read, while the backward walks run
+    const F *zc = zzT + lane;
+    if (f.lf) {
+        wfac_copy(f, f.iD, zzT, (F *)nullptr, (const F *)nullptr, w.nx);
+        zc = f.iD + lane;
     }
     // back substitution y_i = v_i - l_{i+1} y_{i+1}
-    const T lfirst = (T)__ldg(lfT + lane);
+    const T lfirst = (T)lc[0];
     const T lsh = __shfl_down_sync(0xffffffffu, lfirst, 1);
     const T lnext = lane < 31 ? lsh : T(0);
     a = T(1); b = T(0);
-#pragma unroll 4
+#pragma unroll 8
     for (int t = m - 1; t >= 0; --t) {
-        const T ln = t + 1 < m ? (T)__ldg(lfT + (t + 1) * 32 + lane) : lnext;
+        const T ln = t + 1 < m ? (T)lc[(t + 1) * 32] : lnext;
         b = col[t * 33] - ln * b;
         a = -ln * a;
     }
     warp_affine_excl<T, true>(a, b);
     T y = b, ylast = T(0);
-#pragma unroll 4
+#pragma unroll 8
     for (int t = m - 1; t >= 0; --t) {
-        const T ln = t + 1 < m ? (T)__ldg(lfT + (t + 1) * 32 + lane) : lnext;
+        const T ln = t + 1 < m ? (T)lc[(t + 1) * 32] : lnext;
         y = col[t * 33] - ln * y;
         col[t * 33] = y;
         if (t == m - 1) ylast = y;
     }
+    SW_TRACE(223);
     // Sherman-Morrison correction with y_0 (lane 0, t = 0) and y_{n-1}
     // (lane 31, t = m - 1)
     const T y0 = __shfl_sync(0xffffffffu, y, 0);
     const T yn = __shfl_sync(0xffffffffu, ylast, 31);
     const T s = gam * y0 + ec * yn;
-#pragma unroll 4
-    for (int t = 0; t < m; ++t) col[t * 33] -= (T)__ldg(zzT + t * 32 + lane) * s;
+    wfac_wait(f);
+#pragma unroll 16
+    for (int t = 0; t < m; ++t) col[t * 33] -= (T)zc[t * 32] * s;
 }
 
 // store row j of a preconditioner field from the warp's buffer (q_store_row:
@@ -312,17 +414,32 @@ __device__ void wq_store_row(const MemberDev<Pol> &M, typename Pol::q16 *h, floa
     }
 }
 
+// the zonal solve of row j (its factors staged by wfac_issue, or read from
+// global memory)
+template <class Pol>
+__device__ __forceinline__ void wsolve_row(const MemberDev<Pol> &M, const RowView<Pol> &v, int j,
+                                           typename Pol::comp *wb, const WRow w, WFac<typename Pol::fac> &f)
+{
+    typedef typename Pol::comp comp;
+    typedef typename Pol::fac F;
+    const size_t row = (size_t)j * M.nx;
+    wfac_wait(f);
+    SW_TRACE(220);
+    const F *lf = f.lf ? (const F *)f.lf : M.lfT + row;
+    const F *iD = f.lf ? (const F *)f.iD : M.invDT + row;
+    wtrisolve<comp, F>(wb, w, lf, iD, M.zzT + row, (comp)v.gam, (comp)v.ec, f);
+}
+
 // the zonal solve (option 3) and the store of the first preconditioner stage
 // of row j, whose input the warp's buffer holds (stage0_finish)
 template <class Pol>
 __device__ void wstage0_finish(const MemberDev<Pol> &M, const RowView<Pol> &v, int j, typename Pol::comp *wb,
-                               const WRow w)
+                               const WRow w, WFac<typename Pol::fac> &f, bool staged)
 {
-    typedef typename Pol::comp comp;
-    const size_t row = (size_t)j * M.nx;
     __syncwarp();
     SW_TRACE(211);
-    if (M.pc >= 3) wtrisolve<comp, typename Pol::fac>(wb, w, M.lfT + row, M.invDT + row, M.zzT + row, (comp)v.gam, (comp)v.ec);
+    if (M.pc >= 3) wsolve_row(M, v, j, wb, w, f);
+    else if (staged) wfac_wait(f);           // options 0-2: the copies still complete
     __syncwarp();
     SW_TRACE(212);
     if (M.nstages == 1) wq_store_row(M, M.e, M.e32, M.e_s, j, wb, w);
@@ -331,17 +448,33 @@ __device__ void wstage0_finish(const MemberDev<Pol> &M, const RowView<Pol> &v, i
     SW_TRACE(213);
 }
 
+// the warp's passes over a row, 4 consecutive points per lane and pass: all
+// loads of a pass are issued before its arithmetic
+template <class Q, class LD, class CP>
+__device__ __forceinline__ void quads(int nx, LD load, CP compute)
+{
+    const int lane = threadIdx.x & 31;
+    for (int i0 = 4 * lane; i0 < nx; i0 += 128) {
+        Q a;
+        load(i0, a);
+        compute(i0, a);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // phases on one row j (one warp); the thread adds its share of the phase's
 // inner products to part (phase_true, phase_ub, precond_stage, phase_le)
 // ---------------------------------------------------------------------------
 template <class Pol, int NP>
 __device__ void wphase_true(const MemberDev<Pol> &M, const RowView<Pol> &v, typename Pol::comp eta, int j,
-                            typename Pol::comp *wb, const WRow w, typename Acc<Pol>::type (&part)[NP])
+                            typename Pol::comp *wb, const WRow w, WFac<typename Pol::fac> &f,
+                            typename Acc<Pol>::type (&part)[NP])
 {
     typedef typename Pol::comp comp;
     const int nx = M.nx, ny = M.ny, lane = threadIdx.x & 31;
     const size_t row = (size_t)j * nx, rs = j > 0 ? row - nx : row;
+    const bool staged = f.lf && M.pc >= 3;
+    if (staged) wfac_issue(f, M.lfT + row, M.invDT + row, nx);
     const RowCoef<double> c = {M.ax + row, M.cx + row, M.bx + row, M.ay + row, M.cy + row, M.by + row,
                                M.ay + rs, M.cy + rs, M.by + rs, M.C + row};
     int srcS, shS, srcN, shN;
@@ -377,19 +510,29 @@ __device__ void wphase_true(const MemberDev<Pol> &M, const RowView<Pol> &v, type
     }
     part[0] += (typename Acc<Pol>::type)rr;
     part[1] += (typename Acc<Pol>::type)RR;
-    wstage0_finish(M, v, j, wb, w);
+    wstage0_finish(M, v, j, wb, w, f, staged);
 }
+
+template <class Pol, int KM>
+struct UbQuad {
+    typename Pol::comp ev[4];
+    typename Pol::vec le4[4], pv4[KM][4], lp4[KM][4];
+    typename Pol::res r4[4];
+    double ph4[4];
+};
 
 template <class Pol, int KM>
 __device__ void wphase_ub(const MemberDev<Pol> &M, const MemberCtl &c, const RowView<Pol> &v,
                           typename Pol::comp eta, int j, typename Pol::comp *wb, const WRow w,
-                          typename Acc<Pol>::type (&part)[2 + 2 * KM])
+                          WFac<typename Pol::fac> &f, typename Acc<Pol>::type (&part)[2 + 2 * KM])
 {
     typedef typename Pol::comp comp;
     typedef typename Pol::vec vec;
     typedef typename Acc<Pol>::type acc_t;
-    const int nx = M.nx, lane = threadIdx.x & 31;
+    const int nx = M.nx;
     const size_t row = (size_t)j * nx;
+    const bool staged = f.lf && M.pc >= 3;
+    if (staged) wfac_issue(f, M.lfT + row, M.invDT + row, nx);
     const int nd = c.nu + 1;                      // directions before the new one
     vec *pn = v.pb + (size_t)phys_slot(c, M.k, nd) * v.vstride;
     vec *Lpn = v.Lpb + (size_t)phys_slot(c, M.k, nd) * v.vstride;
@@ -406,66 +549,75 @@ __device__ void wphase_ub(const MemberDev<Pol> &M, const MemberCtl &c, const Row
     const double beta = c.beta;
     const comp beta_c = (comp)beta;
     double *ph = M.phi + row;
-    for (int i0 = 4 * lane; i0 < nx; i0 += 128) {
-        comp ev[4];
-        vec le4[4], pv4[KM][4], lp4[KM][4];
-        typename Pol::res r4[4];
-        double ph4[4];
-        q4own(eq, i0, ev);
-        ldv4(v.Le + i0, le4);
-        ldv4(v.r + i0, r4);
-        ldv4(ph + i0, ph4);
+    auto load = [&](int i0, UbQuad<Pol, KM> &d) {
+        q4own(eq, i0, d.ev);
+        ldv4(v.Le + i0, d.le4);
+        ldv4(v.r + i0, d.r4);
+        ldv4(ph + i0, d.ph4);
 #pragma unroll
         for (int l = 0; l < KM; ++l) {
             if (l < nd) {
-                ldv4(pl[l] + i0, pv4[l]);
-                ldv4(Lpl[l] + i0, lp4[l]);
+                ldv4(pl[l] + i0, d.pv4[l]);
+                ldv4(Lpl[l] + i0, d.lp4[l]);
             }
         }
+    };
+    auto compute = [&](int i0, UbQuad<Pol, KM> &d) {
         vec ps4[4], ls4[4];
         typename Pol::res rs4[4];
         double phn[4];
         const int p0 = tpos4(w, i0);
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            comp pv = ev[u], lw = (comp)le4[u];
+            comp pv = d.ev[u], lw = (comp)d.le4[u];
 #pragma unroll
             for (int l = 0; l < KM; ++l) {
                 if (l < nd) {
-                    pv += al[l] * (comp)pv4[l][u];
-                    lw += al[l] * (comp)lp4[l][u];
+                    pv += al[l] * (comp)d.pv4[l][u];
+                    lw += al[l] * (comp)d.lp4[l][u];
                 }
             }
             ps4[u] = (vec)pv;
             ls4[u] = (vec)lw;
-            phn[u] = ph4[u] + beta * (double)ps4[u];
-            if constexpr (Pol::kMixed) rs4[u] = (typename Pol::res)((comp)r4[u] + beta_c * ls4[u]);
-            else rs4[u] = (comp)r4[u] + beta * ls4[u];
+            phn[u] = d.ph4[u] + beta * (double)ps4[u];
+            if constexpr (Pol::kMixed) rs4[u] = (typename Pol::res)((comp)d.r4[u] + beta_c * ls4[u]);
+            else rs4[u] = (comp)d.r4[u] + beta * ls4[u];
             const acc_t ra = (acc_t)rs4[u], la = (acc_t)ls4[u];
             part[0] += ra * ra;
             part[1] += la * la;
 #pragma unroll
             for (int l = 0; l < KM; ++l)
-                if (l < nd) part[2 + l] += la * (acc_t)lp4[l][u];
+                if (l < nd) part[2 + l] += la * (acc_t)d.lp4[l][u];
             wb[p0 + 33 * u] = stage0_input(M, v, eta, (comp)rs4[u], i0 + u);
         }
         stv4(pn + i0, ps4);
         stv4(Lpn + i0, ls4);
         stv4(ph + i0, phn);
         stv4(v.r + i0, rs4);
-    }
-    wstage0_finish(M, v, j, wb, w);
+    };
+    quads<UbQuad<Pol, KM>>(nx, load, compute);
+    wstage0_finish(M, v, j, wb, w, f, staged);
 }
+
+template <class Pol>
+struct StQuad {
+    typename Pol::comp xc[6], xn[6], xs[6], rv[4], dg[4];
+    Coef4<typename Pol::coef> k;
+};
 
 // Richardson stage mu >= 1 (precond_stage): reads q_mu on rows j - 1 .. j + 1,
 // writes q_{mu+1} (the last stage writes e)
 template <class Pol>
 __device__ void wprecond_stage(const MemberDev<Pol> &M, const RowView<Pol> &v, typename Pol::comp eta, int mu,
-                               int j, typename Pol::comp *wb, const WRow w)
+                               int j, typename Pol::comp *wb, const WRow w, WFac<typename Pol::fac> &f)
 {
     typedef typename Pol::comp comp;
     typedef typename Pol::coef CT;
-    const int nx = M.nx, ny = M.ny, lane = threadIdx.x & 31;
+    const int nx = M.nx, ny = M.ny;
+    const size_t row = (size_t)j * nx;
+    const bool opt3 = (M.pc >= 3), has_n = j < ny - 1, has_s = j > 0;
+    const bool staged = f.lf && opt3;
+    if (staged) wfac_issue(f, M.lfT + row, M.invDT + row, nx);
     const bool last = (mu == M.nstages - 1);
     const typename Pol::q16 *ih = (mu & 1) ? M.qa : M.qb;
     const float *if32 = (mu & 1) ? M.qa32 : M.qb32;
@@ -474,42 +626,50 @@ __device__ void wprecond_stage(const MemberDev<Pol> &M, const RowView<Pol> &v, t
     float *of32 = last ? M.e32 : ((mu & 1) ? M.qb32 : M.qa32);
     float *os = last ? M.e_s : ((mu & 1) ? M.qb_s : M.qa_s);
     const QRow<Pol> qS = qrow(M, ih, if32, is, j - 1), qX = qrow(M, ih, if32, is, j), qN = qrow(M, ih, if32, is, j + 1);
-    const bool opt3 = (M.pc >= 3), has_n = j < ny - 1, has_s = j > 0;
     const RowCoef<CT> c = coef_of(v);
-    for (int i0 = 4 * lane; i0 < nx; i0 += 128) {
-        comp xc[6], xn[6], xs[6];
-        q6(qX, i0, nx, xc);
-        q6(qN, i0, nx, xn);
-        q6(qS, i0, nx, xs);
-        Coef4<CT> k;
-        coef4(c, i0, nx, !opt3, has_n, has_s, k);
-        comp rv[4], dg[4] = {comp(1), comp(1), comp(1), comp(1)};
-        ldv4(v.r + i0, rv);
+    auto load = [&](int i0, StQuad<Pol> &d) {
+        q6(qX, i0, nx, d.xc);
+        q6(qN, i0, nx, d.xn);
+        q6(qS, i0, nx, d.xs);
+        coef4(c, i0, nx, !opt3, has_n, has_s, d.k);
+        ldv4(v.r + i0, d.rv);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) d.dg[u] = comp(1);
         if (!opt3) {
             CT d4[4];
             ldg4(v.diag + i0, d4);
 #pragma unroll
-            for (int u = 0; u < 4; ++u) dg[u] = (comp)d4[u];
+            for (int u = 0; u < 4; ++u) d.dg[u] = (comp)d4[u];
         }
+    };
+    auto compute = [&](int i0, StQuad<Pol> &d) {
         comp y[4];
-        apply4(k, xc, xn, xs, has_n, has_s, y);
+        apply4(d.k, d.xc, d.xn, d.xs, has_n, has_s, y);
         const int p0 = tpos4(w, i0);
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const comp xv = xc[u + 1];
-            wb[p0 + 33 * u] = opt3 ? xv + eta * (y[u] - rv[u]) : xv + (comp)M.omega * (rv[u] - y[u]) / dg[u];
+            const comp xv = d.xc[u + 1];
+            wb[p0 + 33 * u] = opt3 ? xv + eta * (y[u] - d.rv[u]) : xv + (comp)M.omega * (d.rv[u] - y[u]) / d.dg[u];
         }
-    }
+    };
+    quads<StQuad<Pol>>(nx, load, compute);
     __syncwarp();
     SW_TRACE(311);
-    const size_t row = (size_t)j * nx;
-    if (opt3) wtrisolve<comp, typename Pol::fac>(wb, w, M.lfT + row, M.invDT + row, M.zzT + row, (comp)v.gam, (comp)v.ec);
+    if (opt3) wsolve_row(M, v, j, wb, w, f);
     __syncwarp();
     SW_TRACE(312);
     wq_store_row(M, oh, of32, os, j, wb, w);
     __syncwarp();
     SW_TRACE(313);
 }
+
+template <class Pol, int KM>
+struct LeQuad {
+    typename Pol::comp xc[6], xn[6], xs[6];
+    Coef4<typename Pol::coef> k;
+    typename Pol::res r4[4];
+    typename Pol::vec lp4[KM][4];
+};
 
 // L(e) of row j into the row's L e and the inner products <Le,Le>, <r,Le>,
 // <Le,Lp_l>, <r,Lp_l> (phase_le)
@@ -521,7 +681,7 @@ __device__ void wphase_le(const MemberDev<Pol> &M, const MemberCtl &c, const Row
     typedef typename Pol::vec vec;
     typedef typename Pol::coef CT;
     typedef typename Acc<Pol>::type acc_t;
-    const int nx = M.nx, ny = M.ny, lane = threadIdx.x & 31;
+    const int nx = M.nx, ny = M.ny;
     const int nd = c.nu + 1;
     const QRow<Pol> qS = qrow(M, M.e, M.e32, M.e_s, j - 1), qX = qrow(M, M.e, M.e32, M.e_s, j),
                     qN = qrow(M, M.e, M.e32, M.e_s, j + 1);
@@ -530,49 +690,50 @@ __device__ void wphase_le(const MemberDev<Pol> &M, const MemberCtl &c, const Row
     const vec *Lpl[KM];
 #pragma unroll
     for (int l = 0; l < KM; ++l) Lpl[l] = v.Lpb + (size_t)phys_slot(c, M.k, l < nd ? l : 0) * v.vstride;
-    for (int i0 = 4 * lane; i0 < nx; i0 += 128) {
-        comp xc[6], xn[6], xs[6];
-        q6(qX, i0, nx, xc);
-        q6(qN, i0, nx, xn);
-        q6(qS, i0, nx, xs);
-        Coef4<CT> k;
-        coef4(cf, i0, nx, true, has_n, has_s, k);
-        typename Pol::res r4[4];
-        vec lp4[KM][4];
-        ldv4(v.r + i0, r4);
+    auto load = [&](int i0, LeQuad<Pol, KM> &d) {
+        q6(qX, i0, nx, d.xc);
+        q6(qN, i0, nx, d.xn);
+        q6(qS, i0, nx, d.xs);
+        coef4(cf, i0, nx, true, has_n, has_s, d.k);
+        ldv4(v.r + i0, d.r4);
 #pragma unroll
         for (int l = 0; l < KM; ++l)
-            if (l < nd) ldv4(Lpl[l] + i0, lp4[l]);
+            if (l < nd) ldv4(Lpl[l] + i0, d.lp4[l]);
+    };
+    auto compute = [&](int i0, LeQuad<Pol, KM> &d) {
         comp y[4];
-        apply4(k, xc, xn, xs, has_n, has_s, y);
+        apply4(d.k, d.xc, d.xn, d.xs, has_n, has_s, y);
         vec le4[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) le4[u] = (vec)y[u];
         stv4(v.Le + i0, le4);
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const acc_t la = (acc_t)le4[u], rv = (acc_t)r4[u];
+            const acc_t la = (acc_t)le4[u], rv = (acc_t)d.r4[u];
             part[0] += la * la;
             part[1] += rv * la;
 #pragma unroll
             for (int l = 0; l < KM; ++l) {
                 if (l < nd) {
-                    part[2 + l] += la * (acc_t)lp4[l][u];
-                    part[2 + KM + l] += rv * (acc_t)lp4[l][u];
+                    part[2 + l] += la * (acc_t)d.lp4[l][u];
+                    part[2 + KM + l] += rv * (acc_t)d.lp4[l][u];
                 }
             }
         }
-    }
+    };
+    quads<LeQuad<Pol, KM>>(nx, load, compute);
     SW_TRACE(111);
 }
 
 // the first stage of option 3 from the stored r (phase_prec0)
 template <class Pol>
 __device__ void wphase_prec0(const MemberDev<Pol> &M, const RowView<Pol> &v, typename Pol::comp eta, int j,
-                             typename Pol::comp *wb, const WRow w)
+                             typename Pol::comp *wb, const WRow w, WFac<typename Pol::fac> &f)
 {
     typedef typename Pol::comp comp;
     const int lane = threadIdx.x & 31;
+    const bool staged = f.lf && M.pc >= 3;
+    if (staged) wfac_issue(f, M.lfT + (size_t)j * M.nx, M.invDT + (size_t)j * M.nx, M.nx);
     for (int i0 = 4 * lane; i0 < M.nx; i0 += 128) {
         typename Pol::res r4[4];
         ldv4(v.r + i0, r4);
@@ -580,7 +741,17 @@ __device__ void wphase_prec0(const MemberDev<Pol> &M, const RowView<Pol> &v, typ
 #pragma unroll
         for (int u = 0; u < 4; ++u) wb[p0 + 33 * u] = stage0_input(M, v, eta, (comp)r4[u], i0 + u);
     }
-    wstage0_finish(M, v, j, wb, w);
+    wstage0_finish(M, v, j, wb, w, f, staged);
+}
+
+// shared memory of one warp in the warp-per-row mode: its row buffer, then
+// (when staged) the row's transposed lf and invD and the mbarrier
+template <class Pol>
+__host__ __device__ inline size_t warp_slot_bytes(int nx, bool stage)
+{
+    const size_t wbuf = al16((size_t)wbuf_len(nx) * sizeof(typename Pol::comp));
+    const size_t fac = stage ? al16(2 * (size_t)nx * sizeof(typename Pol::fac)) + 16 : 0;
+    return (wbuf + fac + 127) & ~(size_t)127;
 }
 
 } // namespace sw
