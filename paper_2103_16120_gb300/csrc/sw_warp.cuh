@@ -316,7 +316,7 @@ __device__ __forceinline__ void warp_affine_excl(T &a, T &b)
 // and with each lane walking its chunk of m points serially between two warp
 // scans.
 template <class T, class F>
-__device__ __noinline__ void wtrisolve(T *wb, const WRow w, const F *lfT, const F *invDT, const F *__restrict__ zzT,
+__device__ __forceinline__ void wtrisolve(T *wb, const WRow w, const F *lfT, const F *invDT, const F *__restrict__ zzT,
                                        T gam, T ec, WFac<F> &f)
 {
     const int lane = threadIdx.x & 31, m = w.m;
