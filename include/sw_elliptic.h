@@ -110,13 +110,14 @@ typedef struct {
                             default 0.5 */
     int row_mode;        /* launch shape of the solver kernel: 0 automatic (one
                             thread block per latitude row while the rows fit the
-                            resident blocks, else one warp per row when nx is a
-                            power of two >= 128 and a single grid is solved
-                            without the learned preconditioner, else blocks
-                            cycling over rows); 1 thread blocks only; 2 one warp
-                            per row (SW_ERR_INVALID_ARG where not possible).
-                            The results agree to rounding: the inner products
-                            sum in another order. */
+                            resident blocks, else, in the mixed precisions, one
+                            warp per row when nx is a power of two >= 128 and a
+                            single grid is solved without the learned
+                            preconditioner, else blocks cycling over rows);
+                            1 thread blocks only; 2 one warp per row
+                            (SW_ERR_INVALID_ARG where not possible).  The
+                            results agree to rounding: the inner products sum
+                            in another order. */
 } sw_solve_opts;
 
 typedef struct {

@@ -540,7 +540,11 @@ static sw_status plan_launch(int n, const sw_grid *grids, const sw_solve_opts *o
             P.grid = (int)rows_total; P.cc = levels[lv][0]; P.cs = levels[lv][1]; P.smem = sm_l;
         }
     }
-    if (!P.grid && warp_possible && o->row_mode != 1) {
+    // the automatic choice takes one warp per row for the mixed precisions;
+    // the FP64 solver, bound by FP64 instruction issue, measured no faster
+    // with it (582 against 572 us per iteration at 2048 x 1024)
+    const bool warp_auto = o->prec != SW_PREC_FP64;
+    if (!P.grid && warp_possible && (o->row_mode == 2 || (o->row_mode == 0 && warp_auto))) {
         // more rows than resident blocks, rows of a power of two of at least
         // 128 points: one warp per row (every SM works on as many rows at once
         // as it holds warps), on every SM
