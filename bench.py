@@ -392,7 +392,8 @@ def run_gpu(args):
         return ms, sts, clocks
 
     maxit = 6000
-    mixed = sw.sw_solve_opts_default(k=K_GCR, tol=TOL, prec=sw.SW_PREC_MIXED_FP16, max_iters=maxit)
+    mixed = sw.sw_solve_opts_default(k=K_GCR, tol=TOL, prec=sw.SW_PREC_MIXED_FP16, max_iters=maxit,
+                                     pole_band_rows=args.pole_band, ru_every=args.ru_every)
     fp64 = sw.sw_solve_opts_default(k=K_GCR, tol=TOL, prec=sw.SW_PREC_FP64, max_iters=maxit)
 
     # FP64 reference path first (same steps), then the mixed path with clocks
@@ -529,6 +530,8 @@ def run_gpu(args):
             "config": {"workload": q["label"], "nx": nx, "ny": ny, "tol": TOL, "k": K_GCR,
                        "preconditioner": "semi-implicit Richardson, 2 iterations (option 3); learned arm beside",
                        "precision": "mixed-fp16",
+                       "pole_band_rows": "automatic (the paper's angular width)" if args.pole_band < 0 else args.pole_band,
+                       "ru_every": args.ru_every,
                        "l2": f"inputs larger than L2 ({nsets} resident coefficient sets, {nsets * set_bytes / 1e9:.1f} GB)",
                        "parallelism": f"replicas x{world}"},
             "fp64_gcr": {"value": v64, "unit": "solves/s", "ms_per_step": ms64 / args.steps,
@@ -924,6 +927,10 @@ def main():
     ap.add_argument("--workload", default="seq2048",
                     choices=["seq2048", "seq512", "learned256", "ensemble64", "swe512", "oracle"])
     ap.add_argument("--no-learned", action="store_true", help="seq2048: leave the learned arm out")
+    ap.add_argument("--pole-band", type=int, default=-1,
+                    help="seq2048/seq512 mixed arm: FP32 rows at each pole (-1: the paper's angular width)")
+    ap.add_argument("--ru-every", type=int, default=0,
+                    help="seq2048/seq512 mixed arm: FP64 true residual every N iterations (0: at the exit test)")
     ap.add_argument("--samples", type=int, default=20000, help="learned256: training triples")
     ap.add_argument("--epochs", type=int, default=4, help="learned256: training epochs")
     args = ap.parse_args()
