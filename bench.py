@@ -374,6 +374,9 @@ def run_gpu(args):
         run_steps(opts, phi, 0, W, wbuf)
         torch.cuda.synchronize()
         checked(wbuf, W)
+        if opts.split_r0:
+            # Phi_hat of Eq. 14 refreshed once, from the last warm-up solution
+            sw.sw_split_refresh(g, phi)
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         if world > 1:
             torch.distributed.barrier()
@@ -393,7 +396,8 @@ def run_gpu(args):
 
     maxit = 6000
     mixed = sw.sw_solve_opts_default(k=K_GCR, tol=TOL, prec=sw.SW_PREC_MIXED_FP16, max_iters=maxit,
-                                     pole_band_rows=args.pole_band, ru_every=args.ru_every)
+                                     pole_band_rows=args.pole_band, ru_every=args.ru_every,
+                                     split_r0=int(args.split_r0))
     fp64 = sw.sw_solve_opts_default(k=K_GCR, tol=TOL, prec=sw.SW_PREC_FP64, max_iters=maxit)
 
     # FP64 reference path first (same steps), then the mixed path with clocks
@@ -532,6 +536,8 @@ def run_gpu(args):
                        "precision": "mixed-fp16",
                        "pole_band_rows": "automatic (the paper's angular width)" if args.pole_band < 0 else args.pole_band,
                        "ru_every": args.ru_every,
+                       "initial_residual": "FP32, split fluid thickness (Eq. 14), refreshed before the timed steps"
+                                           if args.split_r0 else "FP64",
                        "l2": f"inputs larger than L2 ({nsets} resident coefficient sets, {nsets * set_bytes / 1e9:.1f} GB)",
                        "parallelism": f"replicas x{world}"},
             "fp64_gcr": {"value": v64, "unit": "solves/s", "ms_per_step": ms64 / args.steps,
@@ -929,6 +935,8 @@ def main():
     ap.add_argument("--no-learned", action="store_true", help="seq2048: leave the learned arm out")
     ap.add_argument("--pole-band", type=int, default=-1,
                     help="seq2048/seq512 mixed arm: FP32 rows at each pole (-1: the paper's angular width)")
+    ap.add_argument("--split-r0", action="store_true",
+                    help="seq2048/seq512 mixed arm: initial residual by the split form of Eq. 14")
     ap.add_argument("--ru-every", type=int, default=0,
                     help="seq2048/seq512 mixed arm: FP64 true residual every N iterations (0: at the exit test)")
     ap.add_argument("--samples", type=int, default=20000, help="learned256: training triples")

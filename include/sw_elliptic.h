@@ -127,6 +127,13 @@ typedef struct {
                             (SW_ERR_INVALID_ARG where not possible).  The
                             results agree to rounding: the inner products sum
                             in another order. */
+    int split_r0;        /* mixed precisions: 1 computes the solve's initial
+                            residual r0 = L(Phi_0) - R in FP32 with the split
+                            fluid thickness of Sec. 4.2, Eq. 14, from the
+                            grid's last sw_split_refresh (SW_ERR_INVALID_ARG
+                            without one); 0 (default) computes it in FP64.
+                            Every later true residual, and so the exit test,
+                            stays FP64. */
 } sw_solve_opts;
 
 typedef struct {
@@ -178,6 +185,31 @@ sw_status sw_grid_get_eta(sw_grid g, double *eta);
 /* y = L(x) (Eq. 10).  prec SW_PREC_FP64: x, y are double; SW_PREC_FP32: float
  * (FP32 coefficients and arithmetic).  x and y must not overlap. */
 sw_status sw_operator_apply(sw_grid g, int prec, const void *x, void *y, void *stream);
+
+/* Split fluid thickness of Sec. 4.2, Eq. 14 (refresh step).  Phi is held as
+ * Phi_hat + Phi_tilde: this call stores Phi_hat = fp32(phi) in the grid with
+ * the derivative parts of its face fluxes, computed in FP64 from Phi_hat and
+ * stored in FP32: on the zonal face (i+1/2, j) the difference
+ * Phi_hat[i+1] - Phi_hat[i] and the cross sum Phi_hat[i,j+1] + Phi_hat[i+1,j+1]
+ * - Phi_hat[i,j-1] - Phi_hat[i+1,j-1]; on the meridional face (i, j+1/2) the
+ * difference Phi_hat[j+1] - Phi_hat[j] and the cross sum Phi_hat[i+1,j] +
+ * Phi_hat[i+1,j+1] - Phi_hat[i-1,j] - Phi_hat[i-1,j+1] (with the operator's
+ * periodic and across-pole continuation).  These are the paper's stored
+ * derivatives of Phi_hat with the grid spacings folded into the face
+ * coefficients.  phi: device FP64 [ny][nx].  Allocates 20 bytes per point on
+ * the first call (SW_ERR_OOM if that fails); the paper refreshes every 100
+ * solves. */
+sw_status sw_split_refresh(sw_grid g, const double *phi, void *stream);
+
+/* r = L(Phi) - R with L evaluated in FP32 by Eq. 14 (the difference with R
+ * taken in FP64, r stored as float): Phi_tilde = fp32(phi - Phi_hat), the
+ * flux derivative parts as the stored ones of Phi_hat plus those of
+ * Phi_tilde in FP32, the B and C terms on Phi_hat + Phi_tilde in FP32, the
+ * face coefficients of the grid's FP32 copies.  phi, R: device FP64;
+ * r: device float; all [ny][nx].  SW_ERR_INVALID_ARG before the first
+ * sw_split_refresh.  A refresh survives new coefficients: Phi_hat belongs
+ * to the state, not to the operator. */
+sw_status sw_split_residual(sw_grid g, const double *phi, const double *R, float *r, void *stream);
 
 /* q = P^{-1}(r), the preconditioner o->pc with o->n_richardson iterations
  * (Sec. 2.3, Eq. 13).  FP64 when o->prec is SW_PREC_FP64 (r, q double),

@@ -144,6 +144,21 @@ def sw_operator_apply(g: Grid, x, y, stream=None) -> None:
            "sw_operator_apply")
 
 
+def sw_split_refresh(g: Grid, phi, stream=None) -> None:
+    """Store Phi_hat = fp32(phi) and its flux derivative parts (Sec. 4.2, Eq. 14)."""
+    import torch
+    _check(load().sw_split_refresh(g.handle, _ptr(phi, torch.float64, (g.ny, g.nx)), _stream(stream)),
+           "sw_split_refresh")
+
+
+def sw_split_residual(g: Grid, phi, R, r, stream=None) -> None:
+    """r = L(phi) - R with L in FP32 by the split form of Eq. 14 (r float32)."""
+    import torch
+    shp = (g.ny, g.nx)
+    _check(load().sw_split_residual(g.handle, _ptr(phi, torch.float64, shp), _ptr(R, torch.float64, shp),
+                                    _ptr(r, torch.float32, shp), _stream(stream)), "sw_split_residual")
+
+
 def sw_precond_apply(g: Grid, opts: SolveOpts, r, q, stream=None) -> None:
     import torch
     dt = torch.float64 if opts.prec == SW_PREC_FP64 else torch.float32

@@ -28,7 +28,7 @@ EXPORTS = (
     "sw_model_features", "sw_model_forward", "sw_model_loss_grad", "sw_model_train_step", "sw_model_apply",
     "sw_model_target", "sw_ensemble_solve_async", "sw_debug_barrier",
     "sw_swe_create", "sw_swe_destroy", "sw_swe_set_state", "sw_swe_set_history", "sw_swe_get_state",
-    "sw_swe_explicit", "sw_swe_step",
+    "sw_swe_explicit", "sw_swe_step", "sw_split_refresh", "sw_split_residual",
 )
 SW_MODEL_PARAMS = 158369
 SW_NOALLOC_SCRATCH_BYTES = 16 << 20
@@ -40,7 +40,8 @@ class SolveOpts(C.Structure):
                 ("prec", C.c_int), ("pole_band_rows", C.c_int), ("ru_every", C.c_int),
                 ("threads_per_row", C.c_int),
                 ("res_history", C.c_void_p), ("row_residual", C.c_void_p),
-                ("model", C.c_void_p), ("fb_ratio", C.c_double), ("row_mode", C.c_int)]
+                ("model", C.c_void_p), ("fb_ratio", C.c_double), ("row_mode", C.c_int),
+                ("split_r0", C.c_int)]
 
 
 class SolveStats(C.Structure):

@@ -49,6 +49,11 @@ struct sw_grid_s {
     // of a power of two of at least 128 points; null otherwise)
     double *lfT, *invDT, *zzT;
     float *lf32T, *invD32T, *zz32T;
+    // split fluid thickness (Sec. 4.2, Eq. 14): Phi_hat and its derivative
+    // parts, allocated by the first sw_split_refresh
+    void *split_mem;
+    float *shat, *sdx, *scx, *sdy, *scy;
+    bool split_valid;
     bool has_coeffs;
     double eta_explicit;           // > 0 when chosen by sw_grid_set_eta
     // solver workspace
@@ -178,6 +183,7 @@ extern "C" sw_status sw_grid_destroy(sw_grid g)
 {
     if (!g) return fail(SW_ERR_INVALID_ARG, "sw_grid_destroy: NULL grid");
     cudaFree(g->cmem);
+    if (g->split_mem) cudaFree(g->split_mem);
     cudaFree(g->blk);
     cudaFree(g->desc);
     cudaFreeHost(g->h_desc);
@@ -241,6 +247,7 @@ static sw_status check_opts(const sw_solve_opts *o, bool solve)
         return fail(SW_ERR_INVALID_ARG, "threads_per_row must be 0 or a multiple of 32 up to 256");
     if (!std::isfinite(o->eta)) return fail(SW_ERR_INVALID_ARG, "eta must be finite");
     if (o->row_mode < 0 || o->row_mode > 2) return fail(SW_ERR_INVALID_ARG, "row_mode must be 0, 1 or 2");
+    if (o->split_r0 < 0 || o->split_r0 > 1) return fail(SW_ERR_INVALID_ARG, "split_r0 must be 0 or 1");
     return SW_OK;
 }
 
@@ -433,6 +440,19 @@ static void fill_member(sw_grid g, const sw_solve_opts *o, const double *R, doub
     M.part = (double *)(w + L.part);
     M.hist = o->res_history;
     M.rowres = o->row_residual;
+    M.split = (Pol::kMixed && o->split_r0) ? 1 : 0;
+    M.shat = g->shat; M.sdx = g->sdx; M.scx = g->scx; M.sdy = g->sdy; M.scy = g->scy;
+}
+
+// the split initial residual needs a mixed precision, a refresh of this grid
+// and rows of a multiple of 8 points
+static sw_status check_split(const sw_grid_s *g, const sw_solve_opts *o)
+{
+    if (!o->split_r0) return SW_OK;
+    if (o->prec == SW_PREC_FP64) return fail(SW_ERR_INVALID_ARG, "split_r0 is for the mixed precisions");
+    if (!g->split_valid) return fail(SW_ERR_INVALID_ARG, "split_r0: call sw_split_refresh on the grid first");
+    if (g->nx % 8) return fail(SW_ERR_INVALID_ARG, "split_r0: nx must be a multiple of 8");
+    return SW_OK;
 }
 
 static sw_status upload_member(sw_grid g, const sw_solve_opts *o, const double *R, double *phi, cudaStream_t s,
@@ -645,6 +665,7 @@ static sw_status check_members(int n, const sw_grid *grids, const sw_solve_opts 
             if (grids[q] == g) return fail(SW_ERR_INVALID_ARG, "the member grids must be distinct");
         if (n > 1 && (o->res_history || o->row_residual))
             return fail(SW_ERR_INVALID_ARG, "res_history / row_residual are for single solves");
+        if (sw_status sst = check_split(g, o)) return sst;
         max_nx = std::max(max_nx, g->nx);
     }
     return SW_OK;
@@ -720,6 +741,7 @@ static sw_status solve_members(int n, const sw_grid *grids, const sw_solve_opts 
             if (grids[q] == g) return fail(SW_ERR_INVALID_ARG, "the member grids must be distinct");
         if (n > 1 && (o->res_history || o->row_residual))
             return fail(SW_ERR_INVALID_ARG, "res_history / row_residual are for single solves");
+        if (sw_status sst = check_split(g, o)) return sst;
         max_nx = std::max(max_nx, g->nx);
     }
     if (n == 1 && o->pc != SW_PC_LEARNED) {
@@ -864,6 +886,7 @@ extern "C" sw_status sw_gcr_solve_noalloc(sw_grid g, const sw_solve_opts *o, con
     int dev = -1;
     CK(cudaGetDevice(&dev));
     if (g->device != dev) return fail(SW_ERR_INVALID_ARG, "sw_gcr_solve_noalloc: the grid belongs to another device");
+    if ((st = check_split(g, o))) return st;
     const size_t need = ws_layout(g, o->prec, o->k).total;
     if (need > SW_NOALLOC_SCRATCH_BYTES) {
         char msg[200];
@@ -998,6 +1021,42 @@ extern "C" sw_status sw_ensemble_solve_async(int n, const sw_grid *grids, const 
     }
     CK(launch_init_members(lead->desc, n, s));
     CK(launch_gcr(o->prec, o->k, P.minb, P.warp, lead->desc, P.grid, max_nx, P.threads, P.smem, s));
+    return SW_OK;
+}
+
+// ---------------------------------------------------------------------------
+// split fluid thickness (Sec. 4.2, Eq. 14)
+// ---------------------------------------------------------------------------
+extern "C" sw_status sw_split_refresh(sw_grid g, const double *phi, void *stream)
+{
+    if (!g || !phi) return fail(SW_ERR_INVALID_ARG, "sw_split_refresh: NULL argument");
+    if (g->nx % 8) return fail(SW_ERR_INVALID_ARG, "sw_split_refresh: nx must be a multiple of 8");
+    if (!g->split_mem) {
+        const size_t b = al(g->N * 4);
+        void *p = nullptr;
+        cudaError_t e = cudaMalloc(&p, 5 * b);
+        if (e != cudaSuccess) { cudaGetLastError(); return fail(SW_ERR_OOM, "sw_split_refresh: device allocation failed"); }
+        g->split_mem = p;
+        char *c = (char *)p;
+        g->shat = (float *)c; g->sdx = (float *)(c + b); g->scx = (float *)(c + 2 * b);
+        g->sdy = (float *)(c + 3 * b); g->scy = (float *)(c + 4 * b);
+    }
+    SplitRefreshArgs a{g->nx, g->ny, phi, g->shat, g->sdx, g->scx, g->sdy, g->scy};
+    CK(launch_split_refresh(a, (cudaStream_t)stream));
+    g->split_valid = true;
+    return SW_OK;
+}
+
+extern "C" sw_status sw_split_residual(sw_grid g, const double *phi, const double *R, float *r, void *stream)
+{
+    if (!g || !phi || !R || !r) return fail(SW_ERR_INVALID_ARG, "sw_split_residual: NULL argument");
+    if (!g->has_coeffs) return fail(SW_ERR_INVALID_ARG, "sw_split_residual: coefficients not set");
+    if (!g->split_valid) return fail(SW_ERR_INVALID_ARG, "sw_split_residual: call sw_split_refresh first");
+    if (((uintptr_t)phi & 15) || ((uintptr_t)R & 15) || ((uintptr_t)r & 15))
+        return fail(SW_ERR_INVALID_ARG, "sw_split_residual: phi, R and r must be 16-byte aligned");
+    SplitResidualArgs a{g->nx, g->ny, phi, R, r, g->wax, g->wcx, g->wbx, g->way, g->wcy, g->wby, g->wC,
+                        g->shat, g->sdx, g->scx, g->sdy, g->scy};
+    CK(launch_split_residual(a, (cudaStream_t)stream));
     return SW_OK;
 }
 

@@ -121,6 +121,10 @@ struct MemberDev {
     double *part;                   // [2][NSLOT][ny] block partial sums (phase parity)
     double *hist;                   // optional residual history
     double *rowres;                 // optional per-row final residual
+    // split fluid thickness (Sec. 4.2, Eq. 14): the initial residual in FP32
+    // from Phi_hat and its stored derivative parts (mixed policies)
+    int split, pad_split_;
+    const float *shat, *sdx, *scx, *sdy, *scy;
 };
 
 // per-member GCR state.  Every block of the member keeps an identical copy in

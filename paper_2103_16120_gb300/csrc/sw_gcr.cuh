@@ -35,7 +35,7 @@
 // step share one pass: three phases per iteration.
 #pragma once
 
-#include "sw_warp.cuh"
+#include "sw_split.cuh"
 #include "sw_internal.h"
 
 namespace sw {
@@ -710,7 +710,21 @@ __global__ void __launch_bounds__(MAX_THREADS, MINB) k_gcr(const EnsDesc *__rest
                 view_const_global(M, j, v);
                 view_state_global(M, j, v);
                 switch (s_c.phase) {
-                case PH_TRUE: wphase_true<Pol, NP>(M, v, eta, j, wb, wr, wf, part); break;
+                case PH_TRUE:
+                    if constexpr (Pol::kMixed) {
+                        if (M.split && s_c.init) {
+                            // the initial residual by Eq. 14 (split fluid thickness)
+                            const bool staged = wf.lf && M.pc >= 3;
+                            if (staged) wfac_issue(wf, M.lfT + (size_t)j * nx, M.invDT + (size_t)j * nx, nx);
+                            const SplitState S = {M.shat, M.sdx, M.scx, M.sdy, M.scy};
+                            split_true_row<Pol, NP>(M, S, v, eta, j, threadIdx.x & 31, 32, part,
+                                                    [&](int i, comp x) { wb[tpos(wr, i)] = x; });
+                            wstage0_finish(M, v, j, wb, wr, wf, staged);
+                            break;
+                        }
+                    }
+                    wphase_true<Pol, NP>(M, v, eta, j, wb, wr, wf, part);
+                    break;
                 case PH_UB: wphase_ub<Pol, KM>(M, s_c, v, eta, j, wb, wr, wf, part); break;
                 case PH_PREC: wprecond_stage<Pol>(M, v, eta, s_c.stage, j, wb, wr, wf); break;
                 case PH_PREC0: wphase_prec0<Pol>(M, v, eta, j, wb, wr, wf); break;
@@ -728,7 +742,20 @@ __global__ void __launch_bounds__(MAX_THREADS, MINB) k_gcr(const EnsDesc *__rest
                 if (j == j0) v = vc;
                 else { view_const_global(M, j, v); view_state_global(M, j, v); }
                 switch (s_c.phase) {
-                case PH_TRUE: phase_true<Pol, NP>(M, v, eta, j, ws, part); break;
+                case PH_TRUE:
+                    if constexpr (Pol::kMixed) {
+                        if (M.split && s_c.init) {
+                            // the initial residual by Eq. 14 (split fluid thickness)
+                            comp *sb = (comp *)(ws + sb_offset<Pol>(nx));
+                            const SplitState S = {M.shat, M.sdx, M.scx, M.sdy, M.scy};
+                            split_true_row<Pol, NP>(M, S, v, eta, j, threadIdx.x, blockDim.x, part,
+                                                    [&](int i, comp x) { sb[pidx(i)] = x; });
+                            stage0_finish(M, v, j, ws);
+                            break;
+                        }
+                    }
+                    phase_true<Pol, NP>(M, v, eta, j, ws, part);
+                    break;
                 case PH_UB: phase_ub<Pol, KM>(M, s_c, v, eta, j, ws, part); break;
                 case PH_PREC: precond_stage<Pol>(M, v, eta, s_c.stage, j, ws); break;
                 case PH_PREC0: phase_prec0<Pol>(M, v, eta, j, ws); break;

@@ -50,6 +50,22 @@ struct GridGeom {
 };
 GridGeom grid_geom(const ::sw_grid_s *g);
 
+// split fluid thickness of Sec. 4.2, Eq. 14 (sw_solver.cu)
+struct SplitRefreshArgs {
+    int nx, ny;
+    const double *phi;
+    float *hat, *dx, *cx, *dy, *cy;
+};
+struct SplitResidualArgs {
+    int nx, ny;
+    const double *phi, *R;
+    float *r;
+    const float *wax, *wcx, *wbx, *way, *wcy, *wby, *wC;
+    const float *hat, *dx, *cx, *dy, *cy;
+};
+cudaError_t launch_split_refresh(const SplitRefreshArgs &a, cudaStream_t s);
+cudaError_t launch_split_residual(const SplitResidualArgs &a, cudaStream_t s);
+
 cudaError_t launch_faces(const FaceArgs &a, int threads, cudaStream_t s);
 cudaError_t launch_factor(const FactorArgs &a, bool fp64, int threads, cudaStream_t s);
 size_t gcr_smem_bytes(int prec, int max_nx, int k, int cache_const, int cache_state);

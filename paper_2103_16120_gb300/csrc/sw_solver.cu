@@ -173,6 +173,62 @@ __global__ void k_unpack_e(const MemberDev<Pol> *Mp, float *q)
     for (int i = threadIdx.x; i < M.nx; i += blockDim.x) q[(size_t)j * M.nx + i] = (float)q_load(M, M.e, M.e32, sc, j, i);
 }
 
+// ---------------------------------------------------------------------------
+// split fluid thickness (Sec. 4.2, Eq. 14): refresh and standalone residual
+// ---------------------------------------------------------------------------
+// Phi_hat = fp32(Phi) of row j and the derivative parts of its face fluxes,
+// computed in FP64 from the FP32 values and rounded to FP32 (sw_split.cuh)
+__global__ void __launch_bounds__(MAX_THREADS) k_split_refresh(SplitRefreshArgs a)
+{
+    const int nx = a.nx, ny = a.ny, j = blockIdx.x;
+    auto H = [&](int ii, int jj) -> double {
+        if (jj < 0) { jj = 0; ii += nx / 2; }
+        else if (jj >= ny) { jj = ny - 1; ii += nx / 2; }
+        ii %= nx;
+        if (ii < 0) ii += nx;
+        return (double)(float)a.phi[(size_t)jj * nx + ii];
+    };
+    const size_t row = (size_t)j * nx;
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+        a.hat[row + i] = (float)a.phi[row + i];
+        a.dx[row + i] = (float)(H(i + 1, j) - H(i, j));
+        a.cx[row + i] = (float)((H(i, j + 1) + H(i + 1, j + 1)) - (H(i, j - 1) + H(i + 1, j - 1)));
+        a.dy[row + i] = j < ny - 1 ? (float)(H(i, j + 1) - H(i, j)) : 0.f;
+        a.cy[row + i] = j < ny - 1 ? (float)((H(i + 1, j) + H(i + 1, j + 1)) - (H(i - 1, j) + H(i - 1, j + 1))) : 0.f;
+    }
+}
+
+// r = L(Phi) - R with L by Eq. 14 in FP32 (the difference with R in FP64)
+__global__ void __launch_bounds__(128) k_split_residual(SplitResidualArgs a)
+{
+    const SplitOp op = {a.nx, a.ny, a.phi, a.wax, a.wcx, a.wbx, a.way, a.wcy, a.wby, a.wC};
+    const SplitState S = {a.hat, a.dx, a.cx, a.dy, a.cy};
+    const int j = blockIdx.y;
+    const int i0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (i0 >= a.nx) return;
+    float L[4];
+    split_quad(op, S, j, i0, L);
+    const size_t at = (size_t)j * a.nx + i0;
+    double Rv[4];
+    ldg4(a.R + at, Rv);
+    float r[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) r[u] = (float)((double)L[u] - Rv[u]);
+    stv4(a.r + at, r);
+}
+
+cudaError_t launch_split_refresh(const SplitRefreshArgs &a, cudaStream_t s)
+{
+    k_split_refresh<<<a.ny, MAX_THREADS, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_split_residual(const SplitResidualArgs &a, cudaStream_t s)
+{
+    k_split_residual<<<dim3((a.nx / 4 + 127) / 128, a.ny), 128, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
 __global__ void k_fill(double *p, size_t n, double v)
 {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) p[i] = v;
