@@ -371,7 +371,9 @@ def run_gpu(args):
     def timed(opts, K, W, clk=None):
         phi = torch.zeros((ny, nx), dtype=torch.float64, device=dev)
         wbuf, sbuf = sw.stats_buffer(max(W, 1)), sw.stats_buffer(K)
-        run_steps(opts, phi, 0, W, wbuf)
+        wopts = sw.SolveOpts.from_buffer_copy(opts)
+        wopts.split_r0 = 0          # the warm-up steps come before the first refresh
+        run_steps(wopts, phi, 0, W, wbuf)
         torch.cuda.synchronize()
         checked(wbuf, W)
         if opts.split_r0:

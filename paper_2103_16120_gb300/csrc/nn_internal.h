@@ -42,6 +42,14 @@ inline cudaError_t launch_conv_auto(int cin, int cout, bool dgrad, const ConvArg
                                                     : launch_conv(cin, cout, dgrad, a, sms, s);
 }
 cudaError_t launch_wgrad(int cin, int cout, const WgradArgs &a, int sms, cudaStream_t s);
+// the weight gradient on tcgen05 (nn_tc.cu) for the layers it takes
+bool wgrad_tc_supported(int cin, int cout, int W);
+cudaError_t launch_wgrad_tc(int cin, int cout, const WgradArgs &a, int sms, int *err, cudaStream_t s);
+inline cudaError_t launch_wgrad_auto(int cin, int cout, const WgradArgs &a, int sms, int *err, cudaStream_t s)
+{
+    return wgrad_tc_supported(cin, cout, a.W) ? launch_wgrad_tc(cin, cout, a, sms, err, s)
+                                              : launch_wgrad(cin, cout, a, sms, s);
+}
 
 // elementwise and small kernels (nn_ops.cu); shapes are of the fine level
 cudaError_t launch_pool(const __nv_bfloat16 *x, __nv_bfloat16 *y, int B, int H, int W, int C, cudaStream_t s);

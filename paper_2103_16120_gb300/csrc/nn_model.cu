@@ -163,7 +163,7 @@ sw_status backward(sw_model_s *M, int B, int H, int W, const float *target, cuda
     NCK(launch_loss(A.y, target, A.gy16, A.scal + 1, B, H, W, s));
     auto wg = [&](int l, const bf16 *g, const bf16 *x, int b_, int h_, int w_) {
         WgradArgs a{g, x, M->dw[l], M->db[l], b_, h_, w_};
-        return launch_wgrad(LAYER[l].cin_pad, LAYER[l].cout_pad, a, M->sms, s);
+        return launch_wgrad_auto(LAYER[l].cin_pad, LAYER[l].cout_pad, a, M->sms, M->err, s);
     };
     // c6 (32 -> 1, padded to 16 outputs)
     NCK(wg(5, A.gy16, A.a5, B, H, W));
