@@ -47,7 +47,10 @@ __device__ __forceinline__ unsigned long long gtime()
 }
 
 // shared-memory matrix descriptor: start, leading (K) and stride (M/N)
-// byte offsets in 16-byte units, descriptor version 1, no swizzle
+// byte offsets in 16-byte units, descriptor version 1, no swizzle.  In both
+// the K-major and the MN-major no-swizzle layouts the leading offset is the
+// step between core matrices along K and the stride offset the step along
+// M or N.
 __device__ __forceinline__ unsigned long long sdesc(unsigned addr, unsigned lbo, unsigned sbo)
 {
     return (unsigned long long)((addr & 0x3FFFF) >> 4) | ((unsigned long long)((lbo >> 4) & 0x3FFF) << 16) |
@@ -363,49 +366,63 @@ cudaError_t launch_conv_tc(int cin, int cout, bool dgrad, const ConvArgs &a, int
 // ---------------------------------------------------------------------------
 // dW[ky][kx][co][ci] = sum over points p of x[row h + ky - 1][p + kx - 1][ci]
 // g[row h][p][co], with the forward convolution's sphere halo.  As a GEMM
-// D[m][n] = sum_k A[m][k] B[n][k]: m = ci (M = 128, input channels padded
-// with zero planes), n = co (N = COUT) per tap, k = points.  The operands sit
-// in shared memory in the layout the forward kernel stages (one plane per 8
-// channels, a 16-byte row per point), which for this GEMM is the MN-major
-// no-swizzle layout: 8 consecutive MN elements per 16-byte row, 8 rows per K
-// core matrix.  So both operands are read with the transpose bits of the
-// instruction descriptor set, and a longitude tap shift is again a 16-byte
-// start offset.  A block owns one kernel row ky and accumulates its three taps
-// (3 COUT TMEM columns) over all of its work units (one 128-point segment of
-// one latitude row); only at the end are the accumulators read out of TMEM
-// and added to dW.
-constexpr int WG_SLOTS = 3;     // staging slots (two units in flight)
+// D[m][n] = sum_k A[m][k] B[n][k]: m = ci (M = 128), n = co (N = COUT) for
+// each tap, k = points.  The operands sit in shared memory in the layout the
+// forward kernel stages (one plane per 8 channels, a 16-byte row per point),
+// which for this GEMM is the MN-major no-swizzle layout (8 consecutive MN
+// elements per 16-byte row, 8 rows per K core matrix): both are read with
+// the transpose bits of the instruction descriptor set, and a longitude tap
+// shift is a 16-byte start offset.  With fewer than 128 input channels the A
+// operand's upper rows read the next ring slot: those rows of D are never
+// read out.
+//
+// A block works down a strip of WG_STRIP output rows of one 128-point column
+// and accumulates KYS kernel rows (3 KYS taps, 3 KYS COUT TMEM columns) over
+// all of its strips; only at the end are the accumulators read out of TMEM
+// and added to dW.  Input rows sit in a ring (each staged once per strip) and
+// gradient rows in a second one, WG_AHEAD rows ahead of the MMAs; every row's
+// MMAs are committed to one of three mbarriers, and a ring slot is restaged
+// only after the MMAs of the last row that reads it are complete.  Every wait
+// is bounded.
+constexpr int WG_STRIP = 8;     // output rows of one work unit
+constexpr int WG_AHEAD = 2;     // rows staged ahead of the MMAs
 
-template <int CIN, int COUT>
-__host__ __device__ constexpr size_t wg_slot_bytes()
-{
-    return (size_t)16 * TC_P * 16 + (size_t)(COUT / 8) * TC_TW * 16;   // x: 16 planes (M = 128), g
-}
+template <int CIN, int COUT, int KYS>
+struct WgShape {
+    static constexpr int KC = CIN / 8, GC = COUT / 8;
+    static constexpr int XR = WG_AHEAD + KYS + 1;                  // input-row ring slots
+    static constexpr int GR = WG_AHEAD + 2;                        // gradient-row ring slots
+    static constexpr size_t XSLOT = (size_t)KC * TC_P * 16;
+    static constexpr size_t XPAD = (size_t)(16 - KC) * TC_P * 16;  // the last slot's 16-plane read
+    static constexpr size_t GSLOT = (size_t)GC * TC_TW * 16;
+    static constexpr size_t BYTES = XR * XSLOT + XPAD + GR * GSLOT;
+    static constexpr unsigned NCOL = 3 * KYS * COUT;
+};
 
-template <int CIN, int COUT>
+template <int CIN, int COUT, int KYS>
 __global__ void __launch_bounds__(128) k_wgrad_tc(WgradArgs a, int *err)
 {
-    constexpr int KC = CIN / 8, GC = COUT / 8;
-    constexpr unsigned NCOL = 3 * COUT;
-    constexpr unsigned TCOLS = tmem_cols(NCOL);
+    typedef WgShape<CIN, COUT, KYS> S;
+    constexpr unsigned TCOLS = tmem_cols(S::NCOL);
     // BF16 A and B, both MN-major (transpose bits 15 and 16), FP32 accumulator
     constexpr unsigned ID = idesc_bf16(TC_TW, COUT) | (1u << 15) | (1u << 16);
-    constexpr size_t XB = (size_t)16 * TC_P * 16;                     // x part of a slot
-    constexpr size_t SLOTB = wg_slot_bytes<CIN, COUT>();
+    constexpr int NKG = 3 / KYS;                       // groups of kernel rows
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ __align__(8) unsigned long long s_mbar[WG_SLOTS];
+    unsigned char *Xs = smem, *Gs = smem + S::XR * S::XSLOT + S::XPAD;
+    __shared__ __align__(8) unsigned long long s_mbar[3];
     __shared__ unsigned s_tmem;
     __shared__ int s_bad;
     const int H = a.H, W = a.W;
-    const int nseg = W / TC_TW;
-    const long nunits = (long)a.B * H * nseg;
-    const int ky = blockIdx.x % 3, split = blockIdx.x / 3, nsplit = gridDim.x / 3;
+    const int nseg = W / TC_TW, nstrip = (H + WG_STRIP - 1) / WG_STRIP;
+    const long nunits = (long)a.B * nseg * nstrip;
+    const int ky0 = (blockIdx.x % NKG) * KYS;
+    const int split = blockIdx.x / NKG, nsplit = gridDim.x / NKG;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const bool do_bias = a.db && ky == 0;
+    const bool do_bias = a.db && ky0 == 0;
 
     if (threadIdx.x == 0) {
         s_bad = 0;
-        for (int q = 0; q < WG_SLOTS; ++q)
+        for (int q = 0; q < 3; ++q)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_mbar[q])) : "memory");
     }
     if (warp == 0) {
@@ -414,117 +431,139 @@ __global__ void __launch_bounds__(128) k_wgrad_tc(WgradArgs a, int *err)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    // the zero planes of the padded input channels (never written by staging)
-    for (int q = threadIdx.x; q < WG_SLOTS * (16 - KC) * TC_P; q += blockDim.x) {
-        const int slot = q / ((16 - KC) * TC_P), r = q % ((16 - KC) * TC_P);
-        *(uint4 *)(smem + slot * SLOTB + ((size_t)KC * TC_P + r) * 16) = make_uint4(0, 0, 0, 0);
-    }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const unsigned tmem = s_tmem;
-    unsigned par[WG_SLOTS] = {0, 0, 0};
+    unsigned par[3] = {0, 0, 0};
+    bool pend[3] = {false, false, false};
 
-    // stage unit u (x row h + ky - 1 with the sphere halo, g row h) into a slot
-    auto stage = [&](long u, int slot) {
-        const int seg = (int)(u % nseg);
-        const long bh = u / nseg;
-        const int h = (int)(bh % H), b = (int)(bh / H);
-        const int w0 = seg * TC_TW;
-        int hs = h - 1 + ky, shift = 0;
+    auto xslot = [&](int xr) { return Xs + (size_t)((xr + 2 * S::XR) % S::XR) * S::XSLOT; };
+    auto gslot = [&](int h) { return Gs + (size_t)(h % S::GR) * S::GSLOT; };
+    // input row xr (-1 .. H) with the sphere halo: beyond a pole, the pole row
+    // shifted by half a circle
+    auto stage_x = [&](int b, int w0, int xr) {
+        int hs = xr, shift = 0;
         if (hs < 0) { hs = 0; shift = W / 2; }
         else if (hs >= H) { hs = H - 1; shift = W / 2; }
-        unsigned char *xs = smem + (size_t)slot * SLOTB, *gs = xs + XB;
-        for (int q = threadIdx.x; q < TC_P * KC; q += blockDim.x) {
-            const int c = q % KC, pt = q / KC;
+        unsigned char *xs = xslot(xr);
+        for (int q = threadIdx.x; q < TC_P * S::KC; q += blockDim.x) {
+            const int c = q % S::KC, pt = q / S::KC;
             int ws = (w0 - 1 + pt + shift) % W;
             if (ws < 0) ws += W;
             cp16(xs + ((size_t)c * TC_P + pt) * 16, a.x + (((size_t)b * H + hs) * W + ws) * CIN + c * 8);
         }
-        for (int q = threadIdx.x; q < TC_TW * GC; q += blockDim.x) {
-            const int c = q % GC, pt = q / GC;
+    };
+    auto stage_g = [&](int b, int w0, int h) {
+        unsigned char *gs = gslot(h);
+        for (int q = threadIdx.x; q < TC_TW * S::GC; q += blockDim.x) {
+            const int c = q % S::GC, pt = q / S::GC;
             cp16(gs + ((size_t)c * TC_TW + pt) * 16, a.g + (((size_t)b * H + h) * W + w0 + pt) * COUT + c * 8);
         }
-        asm volatile("cp.async.commit_group;" ::: "memory");
     };
-    auto wait_slot = [&](int slot) {
-        const bool okw = mbar_wait(smem_u32(&s_mbar[slot]), par[slot]);
-        par[slot] ^= 1;
+    // the MMAs committed to mbarrier q are complete
+    auto wait_row = [&](int q) {
+        if (!pend[q]) return;
+        const bool okw = mbar_wait(smem_u32(&s_mbar[q]), par[q]);
+        par[q] ^= 1;
+        pend[q] = false;
         if (!okw && lane == 0) atomicExch(&s_bad, 1);
     };
 
     float bsum = 0.f;
-    long nmine = 0;
-    for (long u = split; u < nunits; u += nsplit) ++nmine;
-    if (nmine > 0) stage(split, 0);
-    if (nmine > 1) stage(split + nsplit, 1);
-    bool issued[WG_SLOTS] = {false, false, false};
     unsigned acc = 0;
-    for (long i = 0; i < nmine && !s_bad; ++i) {
-        const int slot = (int)(i % WG_SLOTS);
-        // this unit's copies done (one later group may still be in flight)
-        if (i + 1 < nmine) asm volatile("cp.async.wait_group 1;" ::: "memory");
-        else asm volatile("cp.async.wait_group 0;" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    for (long u = split; u < nunits && !s_bad; u += nsplit) {
+        const int seg = (int)(u % nseg);
+        const int strip = (int)((u / nseg) % nstrip);
+        const int b = (int)(u / nseg / nstrip);
+        const int w0 = seg * TC_TW;
+        const int h0 = strip * WG_STRIP, h1 = min(h0 + WG_STRIP, H);
+        // the previous unit's MMAs read the slots about to be restaged
+        for (int q = 0; q < 3; ++q) wait_row(q);
         __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const unsigned char *xs = smem + (size_t)slot * SLOTB, *gs = xs + XB;
-        if (threadIdx.x == 0) {
-            const unsigned xa = smem_u32(xs), ga = smem_u32(gs);
-#pragma unroll
-            for (int kx = 0; kx < 3; ++kx) {
-#pragma unroll
-                for (int ks = 0; ks < TC_TW / 16; ++ks) {
-                    const unsigned aa = xa + (unsigned)(ks * 16 + kx) * 16;
-                    const unsigned ba = ga + (unsigned)(ks * 16) * 16;
-                    mma_bf16(tmem + (unsigned)(kx * COUT), sdesc(aa, TC_P * 16, 128), sdesc(ba, TC_TW * 16, 128), ID,
-                             acc | (unsigned)ks);
-                }
+        // prologue: the input and gradient rows of the first WG_AHEAD output rows
+        const int hp = min(h0 + WG_AHEAD, h1);
+        for (int xr = h0 + ky0 - 1; xr <= hp - 1 + ky0 + KYS - 2; ++xr) stage_x(b, w0, xr);
+        for (int h = h0; h < hp; ++h) stage_g(b, w0, h);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        for (int h = h0; h < h1; ++h) {
+            // rows for output row h + WG_AHEAD: its newest input row and its
+            // gradient row, into the slots that output row h - 2 read last
+            const int hn = h + WG_AHEAD;
+            if (hn < h1) {
+                if (h - 2 >= h0) wait_row((h - 2) % 3);
+                __syncthreads();
+                stage_x(b, w0, hn + ky0 + KYS - 2);
+                stage_g(b, w0, hn);
             }
-            acc = 1;
-            mma_commit(smem_u32(&s_mbar[slot]));
-        }
-        __syncwarp();
-        issued[slot] = true;
-        if (do_bias && threadIdx.x < COUT) {
-            const int c = threadIdx.x / 8, e = threadIdx.x % 8;
-            for (int p = 0; p < TC_TW; ++p)
-                bsum += __bfloat162float(((const __nv_bfloat16 *)(gs + ((size_t)c * TC_TW + p) * 16))[e]);
-        }
-        // unit i + 2 goes into the slot unit i - 1 used, once its MMAs are done
-        if (i + 2 < nmine) {
-            const int ns = (int)((i + 2) % WG_SLOTS);
-            if (issued[ns]) { wait_slot(ns); issued[ns] = false; }
+            asm volatile("cp.async.commit_group;" ::: "memory");
+            // row h's copies were committed WG_AHEAD groups ago (or in the prologue)
+            asm volatile("cp.async.wait_group %0;" ::"n"(WG_AHEAD) : "memory");
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncthreads();
-            stage(split + (i + 2) * nsplit, ns);
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (s_bad) break;
+            wait_row(h % 3);                       // row h - 3 left this mbarrier's phase
+            if (threadIdx.x == 0) {
+                const unsigned ga = smem_u32(gslot(h));
+#pragma unroll
+                for (int kyl = 0; kyl < KYS; ++kyl) {
+                    const unsigned xa = smem_u32(xslot(h + ky0 + kyl - 1));
+#pragma unroll
+                    for (int kx = 0; kx < 3; ++kx) {
+#pragma unroll
+                        for (int ks = 0; ks < TC_TW / 16; ++ks) {
+                            const unsigned aa = xa + (unsigned)(ks * 16 + kx) * 16;
+                            const unsigned ba = ga + (unsigned)(ks * 16) * 16;
+                            // MN-major: the leading offset steps along K (8 points,
+                            // 128 bytes), the stride offset along MN (one plane)
+                            mma_bf16(tmem + (unsigned)((kyl * 3 + kx) * COUT), sdesc(aa, 128, TC_P * 16),
+                                     sdesc(ba, 128, TC_TW * 16), ID, acc | (unsigned)ks);
+                        }
+                    }
+                }
+                mma_commit(smem_u32(&s_mbar[h % 3]));
+            }
+            __syncwarp();
+            acc = 1;
+            pend[h % 3] = true;
+            if (do_bias) {
+                // bias gradient: thread t adds channel t % COUT over every
+                // (128 / COUT)-th point of the row, all threads at once
+                constexpr int NPART = 128 / COUT;
+                const unsigned char *gs = gslot(h);
+                const int co = threadIdx.x % COUT, c = co / 8, e = co % 8;
+#pragma unroll 8
+                for (int p = threadIdx.x / COUT; p < TC_TW; p += NPART)
+                    bsum += __bfloat162float(((const __nv_bfloat16 *)(gs + ((size_t)c * TC_TW + p) * 16))[e]);
+            }
         }
     }
-    // every MMA done: wait for the slots still in flight
-    for (int q = 0; q < WG_SLOTS; ++q)
-        if (issued[q]) wait_slot(q);
+    for (int q = 0; q < 3; ++q) wait_row(q);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (!s_bad && nmine > 0) {
-        // lanes = input channels (warp w: 32 w .. 32 w + 31), columns = (kx, co)
+    if (!s_bad && acc) {
+        // lanes = input channels (warp w: 32 w .. 32 w + 31), columns = (ky, kx, co)
         const int ci = warp * 32 + lane;
         const unsigned trow = tmem + ((unsigned)(warp * 32) << 16);
-#pragma unroll
-        for (int c0 = 0; c0 < (int)NCOL; c0 += 8) {
+#pragma unroll 4
+        for (int c0 = 0; c0 < (int)S::NCOL; c0 += 8) {
             float v[8];
             tmem_ld8(trow + c0, v);
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
             if (ci < CIN) {
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
-                    const int col = c0 + q, kx = col / COUT, co = col % COUT;
-                    atomicAdd(a.dw + ((size_t)(ky * 3 + kx) * COUT + co) * CIN + ci, v[q]);
+                    const int col = c0 + q, tap = col / COUT, co = col % COUT;
+                    atomicAdd(a.dw + ((size_t)(ky0 * 3 + tap) * COUT + co) * CIN + ci, v[q]);
                 }
             }
         }
     }
-    if (do_bias && threadIdx.x < COUT) atomicAdd(a.db + threadIdx.x, bsum);
+    if (do_bias && acc) atomicAdd(a.db + threadIdx.x % COUT, bsum);
     if (s_bad && threadIdx.x == 0) atomicExch(err, 1);
     asm volatile("cp.async.wait_all;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -534,20 +573,25 @@ __global__ void __launch_bounds__(128) k_wgrad_tc(WgradArgs a, int *err)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS) : "memory");
 }
 
-template <int CIN, int COUT>
+template <int CIN, int COUT, int KYS>
 static cudaError_t wgrad_tc_t(const WgradArgs &a, int sms, int *err, cudaStream_t s)
 {
-    const size_t smem = WG_SLOTS * wg_slot_bytes<CIN, COUT>();
-    cudaError_t e = cudaFuncSetAttribute(k_wgrad_tc<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    typedef WgShape<CIN, COUT, KYS> S;
+    const size_t smem = S::BYTES;
+    cudaError_t e = cudaFuncSetAttribute(k_wgrad_tc<CIN, COUT, KYS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    const long nunits = (long)a.B * a.H * (a.W / TC_TW);
-    long nsplit = sms / 3 > 0 ? sms / 3 : 1;   // about one block per SM over the three kernel rows
+    constexpr int NKG = 3 / KYS;
+    const long nunits = (long)a.B * (a.W / TC_TW) * ((a.H + WG_STRIP - 1) / WG_STRIP);
+    long nsplit = sms / NKG > 0 ? sms / NKG : 1;   // about one block per SM
     if (nsplit > nunits) nsplit = nunits;
-    k_wgrad_tc<CIN, COUT><<<(int)(3 * nsplit), 128, smem, s>>>(a, err);
+    k_wgrad_tc<CIN, COUT, KYS><<<(int)(NKG * nsplit), 128, smem, s>>>(a, err);
     return cudaGetLastError();
 }
 
+// the layers whose weight gradient takes tcgen05: c5 (96 -> 32, all nine taps
+// in one block, 288 TMEM columns) and c4 (128 -> 64, a kernel row per block,
+// 192 columns), rows of a multiple of 128 points
 bool wgrad_tc_supported(int cin, int cout, int W)
 {
     return W % TC_TW == 0 && ((cin == 96 && cout == 32) || (cin == 128 && cout == 64));
@@ -555,8 +599,8 @@ bool wgrad_tc_supported(int cin, int cout, int W)
 
 cudaError_t launch_wgrad_tc(int cin, int cout, const WgradArgs &a, int sms, int *err, cudaStream_t s)
 {
-    if (cin == 96 && cout == 32) return wgrad_tc_t<96, 32>(a, sms, err, s);
-    if (cin == 128 && cout == 64) return wgrad_tc_t<128, 64>(a, sms, err, s);
+    if (cin == 96 && cout == 32) return wgrad_tc_t<96, 32, 3>(a, sms, err, s);
+    if (cin == 128 && cout == 64) return wgrad_tc_t<128, 64, 1>(a, sms, err, s);
     return cudaErrorInvalidValue;
 }
 
