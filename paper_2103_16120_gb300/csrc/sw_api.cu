@@ -547,9 +547,10 @@ static sw_status plan_launch(int n, const sw_grid *grids, const sw_solve_opts *o
     for (int m = 0; m < n; ++m) rows_total += grids[m]->ny;
     // the learned preconditioner ends a launch before every application of
     // the network, so the owner-only vectors cannot live in shared memory
-    const bool warp_possible = n == 1 && o->pc != SW_PC_LEARNED && grids[0]->lfT;
+    bool warp_possible = o->pc != SW_PC_LEARNED;
+    for (int m = 0; m < n; ++m) warp_possible = warp_possible && grids[m]->lfT;
     if (o->row_mode == 2 && !warp_possible)
-        return fail(SW_ERR_INVALID_ARG, "row_mode 2 (one warp per row) needs one grid with nx a power of two >= 128 "
+        return fail(SW_ERR_INVALID_ARG, "row_mode 2 (one warp per row) needs grids with nx a power of two >= 128 "
                                         "and a preconditioner other than the learned one");
     for (int lv = (o->pc == SW_PC_LEARNED ? 1 : 0); lv < 3 && !P.grid && o->row_mode != 2; ++lv) {
         const size_t sm_l = gcr_smem_bytes(o->prec, max_nx, o->k, levels[lv][0], levels[lv][1]);
@@ -582,18 +583,41 @@ static sw_status plan_launch(int n, const sw_grid *grids, const sw_solve_opts *o
         }
         CK(gcr_occupancy(o->prec, o->k, 2, 1, P.threads, P.smem, &bps2));
         const int warps = P.threads / 32;
-        const int need = (grids[0]->ny + warps - 1) / warps;   // blocks that give every row its own warp
+        long need = 0;                                          // blocks that give every row its own warp
+        for (int m = 0; m < n; ++m) need += (grids[m]->ny + warps - 1) / warps;
         // the register budget of one block per SM unless that leaves rows
         // without a warp and two blocks fit
         P.minb = 1;
-        if (bps * sms < need && bps2 > bps) { bps = bps2; P.minb = 2; }
-        if (bps >= 1) {
-            // the same number of blocks on every SM, as few as give every row a
-            // warp, and no more blocks than rows (the block partial sums are
-            // kept per row slot)
-            const int per_sm = std::min(bps, std::max(1, (need + sms - 1) / sms));
-            P.grid = std::min(per_sm * sms, grids[0]->ny);
-            P.nb[0] = P.grid;
+        if ((long)bps * sms < need && bps2 > bps) { bps = bps2; P.minb = 2; }
+        if (bps >= 1 && n <= bps * sms) {
+            if (n == 1) {
+                // the same number of blocks on every SM, as few as give every
+                // row a warp, and no more blocks than rows (the block partial
+                // sums are kept per row slot)
+                const int per_sm = std::min(bps, std::max(1, (int)((need + sms - 1) / sms)));
+                P.grid = std::min(per_sm * sms, grids[0]->ny);
+                P.nb[0] = P.grid;
+            } else {
+                // members share the resident blocks in proportion to their work
+                // (rows per warp x row length x iterations, which grow with nx),
+                // each at most the blocks that give all of its rows a warp
+                const int cap = bps * sms;
+                int used = n;
+                while (used < cap) {
+                    int best = -1;
+                    double bw = 0.0;
+                    for (int m = 0; m < n; ++m) {
+                        const int mcap = std::min(grids[m]->ny, (grids[m]->ny + warps - 1) / warps);
+                        if (P.nb[m] >= mcap) continue;
+                        const double wgt = (double)grids[m]->ny * grids[m]->nx * grids[m]->nx / P.nb[m];
+                        if (wgt > bw) { bw = wgt; best = m; }
+                    }
+                    if (best < 0) break;
+                    ++P.nb[best];
+                    ++used;
+                }
+                P.grid = used;
+            }
             P.warp = 1;
         } else if (o->row_mode == 2) {
             return fail(SW_ERR_INVALID_ARG, "row_mode 2: the warp-per-row kernel does not fit this device");

@@ -161,3 +161,36 @@ def test_one_member_graph_replays_with_new_right_hand_sides():
         assert got.status == sw.SW_OK and got.iterations == ref[t][1]
         assert torch.equal(phi, ref[t][0]) and torch.equal(other, ref[t][0])
         assert sw.stats_from_device(obuf, 1)[0].iterations == ref[t][1]
+
+
+@pytest.mark.parametrize("prec", [sw.SW_PREC_MIXED_FP16, sw.SW_PREC_FP64])
+def test_warp_rows_ensemble_matches_the_oracle_and_block_mode(prec):
+    """An ensemble whose grids all have power-of-two widths runs with one warp
+    per row (row_mode 2; the automatic choice for the mixed precisions),
+    members sharing the resident blocks by work.  Each member reaches the FP64
+    true residual and the oracle's solution, and the thread-block mode (the
+    same method, other reduction groupings) agrees to the tolerance."""
+    import oracle as O
+    spec = [(128, 64, 9101), (128, 64, 9102), (256, 128, 9103), (512, 256, 9104), (256, 96, 9105)]
+    Ps = [synth.problem(nx, ny, seed) for nx, ny, seed in spec]
+    grids = []
+    for (nx, ny, _), P in zip(spec, Ps):
+        g = sw.sw_grid_create(nx, ny)
+        sw.sw_elliptic_set_coeffs(g, *[torch.as_tensor(P[k], device="cuda") for k in sw.COEFF_KEYS])
+        grids.append(g)
+    Rs = [torch.as_tensor(P["R"], device="cuda") for P in Ps]
+    out = {}
+    for mode in (1, 2):
+        o = sw.sw_solve_opts_default(prec=prec, tol=1e-8, max_iters=3000, row_mode=mode)
+        phis = [torch.zeros_like(R) for R in Rs]
+        sts = sw.sw_ensemble_solve(grids, o, Rs, phis)
+        for st in sts:
+            assert st.status == sw.SW_OK and st.true_rel_residual <= 1e-8, st.as_dict()
+        out[mode] = [p.cpu().numpy() for p in phis]
+    for P, x2, x1 in zip(Ps, out[2], out[1]):
+        ref, _ = O.Problem(P).gcr(P["R"], O.Opts(tol=1e-12, max_iters=4000))
+        # both stop at a residual of 1e-8; the conditioning turns that into a
+        # solution error of up to a few 1e-7
+        tol = 1e-6
+        assert np.linalg.norm(x2 - ref) <= tol * np.linalg.norm(ref)
+        assert np.linalg.norm(x2 - x1) <= 2 * tol * np.linalg.norm(ref)
