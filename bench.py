@@ -576,6 +576,25 @@ def _peaks():
         return {}
 
 
+def _oracle_baseline(problems, budget_s: float, what: str):
+    """The FP64 oracle on the host cores over a bounded sample of problems
+    (zero first guess, tol 1e-8): member solves per second."""
+    import oracle as O
+    import oracle.oracle as orc
+    orc.build()
+    cores = cpu_cores()
+    t0 = time.perf_counter()
+    n = 0
+    for P in problems:
+        O.Problem(P).gcr(P["R"], O.Opts(k=K_GCR, tol=TOL, max_iters=4000))
+        n += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": "solves/s", "cores": cores, "kind": "oracle",
+            "sample": f"{what}: {n} of {len(problems)} solved in {dt:.1f} s, OpenMP over rows ({cores} threads)"}
+
+
 def _grid(sw, torch, P, dev):
     ny, nx = P["C"].shape
     g = sw.sw_grid_create(nx, ny)
@@ -625,10 +644,13 @@ def run_learned(args):
     learned.train(m, x0, tg, steps=args.warmup, batch=B, lr=1e-3)
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clk = ClockSampler(0)
+    clk.start()
     a.record(stream)
     learned.train(m, x0, tg, steps=args.steps, batch=B, lr=1e-3, seed=1)
     b.record(stream)
     torch.cuda.synchronize()
+    clocks = clk.stop()
     ms_step = a.elapsed_time(b) / args.steps
     # then train to the end of the epochs asked for
     epochs_steps = max(0, args.epochs * n // B - args.steps - args.warmup)
@@ -663,10 +685,14 @@ def run_learned(args):
                      "data_generation_s": t_data, "final_loss": losses[-1][1] if losses else None},
         "roofline": {"bound": "tensor", "achieved": tflops, "peak": peak, "unit": "TFLOP/s",
                      "frac": tflops / peak, "traffic": None,
-                     "kernel": "training step (k_conv / k_wgrad, mma.sync BF16)",
+                     "kernel": "training step (tcgen05 forward and c4/c5 weight gradients, mma.sync input "
+                               "gradients and the other weight gradients, BF16 operands, FP32 accumulation)",
                      "note": "algorithmic FLOPs of forward + input and weight gradients per step / step time",
-                     "peak_source": "MEASURED_PEAKS.json bf16_tflops (of measured)"},
-        "cpu_baseline": None, "gpu_launches": None,
+                     "peak_source": "measured bf16_tflops (of measured)"},
+        "cpu_baseline": _oracle_baseline([synth.problem(256, 128, 4_000_000 + s_) for s_ in range(2)], 10.0,
+                                         "FP64 oracle option-3 solves of the 256x128 evaluation problems"),
+        "gpu_launches": None,
+        "clocks": clocks,
     }), flush=True)
 
 
@@ -725,11 +751,14 @@ def run_ensemble(args):
         graph.replay()
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clk = ClockSampler(0)
+    clk.start()
     a.record(stream)
     for _ in range(args.steps):
         graph.replay()
     b.record(stream)
     torch.cuda.synchronize()
+    clocks = clk.stop()
     gms = a.elapsed_time(b) / args.steps
     gst = sw.stats_from_device(buf, len(grids))
     if any(s_.status != sw.SW_OK for s_ in gst):
@@ -756,7 +785,9 @@ def run_ensemble(args):
                      "traffic": None, "kernel": "k_gcr<PolF16> (all members, one launch)",
                      "note": "algorithmic bytes (172 B per point per iteration) / ensemble time",
                      "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
-        "cpu_baseline": None, "gpu_launches": 1 * args.steps,
+        "cpu_baseline": _oracle_baseline(Ps, 15.0, "FP64 oracle solves of the ensemble members one after another"),
+        "gpu_launches": 1 * args.steps,
+        "clocks": clocks,
     }), flush=True)
 
 
