@@ -652,6 +652,9 @@ __global__ void __launch_bounds__(MAX_THREADS, MINB) k_gcr(const EnsDesc *__rest
     unsigned char *ws = dsm;
     // warp mode: the warps' row buffers, then the reduction scratch
     constexpr bool wmode = WARP;          // one warp per row (D->warp_rows)
+    // longest zonal-solve chunk (FP32 points per lane) kept in registers: 64
+    // with the register budget of one block per SM, 16 with that of two
+    constexpr int RM = MINB == 1 ? 64 : 16;
     const WRow wr = wrow(nx);
     double *scratch;
     typedef typename Pol::fac fac_t;
@@ -719,15 +722,15 @@ __global__ void __launch_bounds__(MAX_THREADS, MINB) k_gcr(const EnsDesc *__rest
                             const SplitState S = {M.shat, M.sdx, M.scx, M.sdy, M.scy};
                             split_true_row<Pol, NP>(M, S, v, eta, j, threadIdx.x & 31, 32, part,
                                                     [&](int i, comp x) { wb[tpos(wr, i)] = x; });
-                            wstage0_finish(M, v, j, wb, wr, wf, staged);
+                            wstage0_finish<Pol, RM>(M, v, j, wb, wr, wf, staged);
                             break;
                         }
                     }
-                    wphase_true<Pol, NP>(M, v, eta, j, wb, wr, wf, part);
+                    wphase_true<Pol, NP, RM>(M, v, eta, j, wb, wr, wf, part);
                     break;
-                case PH_UB: wphase_ub<Pol, KM>(M, s_c, v, eta, j, wb, wr, wf, part); break;
-                case PH_PREC: wprecond_stage<Pol>(M, v, eta, s_c.stage, j, wb, wr, wf); break;
-                case PH_PREC0: wphase_prec0<Pol>(M, v, eta, j, wb, wr, wf); break;
+                case PH_UB: wphase_ub<Pol, KM, RM>(M, s_c, v, eta, j, wb, wr, wf, part); break;
+                case PH_PREC: wprecond_stage<Pol, RM>(M, v, eta, s_c.stage, j, wb, wr, wf); break;
+                case PH_PREC0: wphase_prec0<Pol, RM>(M, v, eta, j, wb, wr, wf); break;
                 case PH_LE: wphase_le<Pol, KM>(M, s_c, v, j, wr, part); break;
                 case PH_ZERO:
                     for (int i = threadIdx.x & 31; i < nx; i += 32) M.phi[(size_t)j * nx + i] = 0.0;

@@ -378,6 +378,72 @@ __device__ __forceinline__ void wtrisolve(T *wb, const WRow w, const F *lfT, con
     for (int t = 0; t < m; ++t) col[t * 33] -= (T)zc[t * 32] * s;
 }
 
+// The same solve with the lane's chunk of MM points and its multipliers held
+// in registers: the chunk, the multipliers, the inverse pivots and the
+// Sherman-Morrison vector are each read from shared memory once, and the
+// four walks run on registers.  Every value is computed by the same
+// expressions in the same order as in wtrisolve.
+template <class T, class F, int MM>
+__device__ __forceinline__ void wtrisolve_r(T *wb, const WRow w, const F *lfT, const F *invDT,
+                                            const F *__restrict__ zzT, T gam, T ec, WFac<F> &f)
+{
+    const int lane = threadIdx.x & 31;
+    T *col = wb + lane;
+    const F *lc = lfT + lane, *dc = invDT + lane;
+    T x[MM], l[MM];
+#pragma unroll
+    for (int t = 0; t < MM; ++t) {
+        x[t] = col[t * 33];
+        l[t] = (T)lc[t * 32];
+    }
+    // forward elimination u_i = b_i - l_i u_{i-1}
+    T a = T(1), b = T(0);
+#pragma unroll
+    for (int t = 0; t < MM; ++t) {
+        b = x[t] - l[t] * b;
+        a = -l[t] * a;
+    }
+    SW_TRACE(221);
+    warp_affine_excl<T, false>(a, b);
+    T u = b;
+#pragma unroll
+    for (int t = 0; t < MM; ++t) {
+        u = x[t] - l[t] * u;
+        x[t] = u * (T)dc[t * 32];
+    }
+    SW_TRACE(222);
+    const F *zc = zzT + lane;
+    if (f.lf) {
+        wfac_copy(f, f.iD, zzT, (F *)nullptr, (const F *)nullptr, w.nx);
+        zc = f.iD + lane;
+    }
+    // back substitution y_i = v_i - l_{i+1} y_{i+1}
+    const T lsh = __shfl_down_sync(0xffffffffu, l[0], 1);
+    const T lnext = lane < 31 ? lsh : T(0);
+    a = T(1); b = T(0);
+#pragma unroll
+    for (int t = MM - 1; t >= 0; --t) {
+        const T ln = t + 1 < MM ? l[t + 1] : lnext;
+        b = x[t] - ln * b;
+        a = -ln * a;
+    }
+    warp_affine_excl<T, true>(a, b);
+    T y = b;
+#pragma unroll
+    for (int t = MM - 1; t >= 0; --t) {
+        const T ln = t + 1 < MM ? l[t + 1] : lnext;
+        y = x[t] - ln * y;
+        x[t] = y;
+    }
+    SW_TRACE(223);
+    const T y0 = __shfl_sync(0xffffffffu, x[0], 0);
+    const T yn = __shfl_sync(0xffffffffu, x[MM - 1], 31);
+    const T s = gam * y0 + ec * yn;
+    wfac_wait(f);
+#pragma unroll
+    for (int t = 0; t < MM; ++t) col[t * 33] = x[t] - (T)zc[t * 32] * s;
+}
+
 // store row j of a preconditioner field from the warp's buffer (q_store_row:
 // FP64; FP32 on the pole band; else 16-bit with a power-of-two row scale so
 // that the stored magnitudes are at most 1)
@@ -416,7 +482,7 @@ __device__ void wq_store_row(const MemberDev<Pol> &M, typename Pol::q16 *h, floa
 
 // the zonal solve of row j (its factors staged by wfac_issue, or read from
 // global memory)
-template <class Pol>
+template <class Pol, int RM>
 __device__ __forceinline__ void wsolve_row(const MemberDev<Pol> &M, const RowView<Pol> &v, int j,
                                            typename Pol::comp *wb, const WRow w, WFac<typename Pol::fac> &f)
 {
@@ -427,18 +493,29 @@ __device__ __forceinline__ void wsolve_row(const MemberDev<Pol> &M, const RowVie
     SW_TRACE(220);
     const F *lf = f.lf ? (const F *)f.lf : M.lfT + row;
     const F *iD = f.lf ? (const F *)f.iD : M.invDT + row;
-    wtrisolve<comp, F>(wb, w, lf, iD, M.zzT + row, (comp)v.gam, (comp)v.ec, f);
+    const comp gam = (comp)v.gam, ec = (comp)v.ec;
+    // chunks of up to RM FP32 points (RM / 4 FP64 points) in registers
+    constexpr int rmax = sizeof(comp) == 4 ? RM : RM / 4;
+    switch (w.m) {
+    case 4: if constexpr (rmax >= 4) { wtrisolve_r<comp, F, 4>(wb, w, lf, iD, M.zzT + row, gam, ec, f); return; } break;
+    case 8: if constexpr (rmax >= 8) { wtrisolve_r<comp, F, 8>(wb, w, lf, iD, M.zzT + row, gam, ec, f); return; } break;
+    case 16: if constexpr (rmax >= 16) { wtrisolve_r<comp, F, 16>(wb, w, lf, iD, M.zzT + row, gam, ec, f); return; } break;
+    case 32: if constexpr (rmax >= 32) { wtrisolve_r<comp, F, 32>(wb, w, lf, iD, M.zzT + row, gam, ec, f); return; } break;
+    case 64: if constexpr (rmax >= 64) { wtrisolve_r<comp, F, 64>(wb, w, lf, iD, M.zzT + row, gam, ec, f); return; } break;
+    default: break;
+    }
+    wtrisolve<comp, F>(wb, w, lf, iD, M.zzT + row, gam, ec, f);
 }
 
 // the zonal solve (option 3) and the store of the first preconditioner stage
 // of row j, whose input the warp's buffer holds (stage0_finish)
-template <class Pol>
+template <class Pol, int RM>
 __device__ void wstage0_finish(const MemberDev<Pol> &M, const RowView<Pol> &v, int j, typename Pol::comp *wb,
                                const WRow w, WFac<typename Pol::fac> &f, bool staged)
 {
     __syncwarp();
     SW_TRACE(211);
-    if (M.pc >= 3) wsolve_row(M, v, j, wb, w, f);
+    if (M.pc >= 3) wsolve_row<Pol, RM>(M, v, j, wb, w, f);
     else if (staged) wfac_wait(f);           // options 0-2: the copies still complete
     __syncwarp();
     SW_TRACE(212);
@@ -465,7 +542,7 @@ __device__ __forceinline__ void quads(int nx, LD load, CP compute)
 // phases on one row j (one warp); the thread adds its share of the phase's
 // inner products to part (phase_true, phase_ub, precond_stage, phase_le)
 // ---------------------------------------------------------------------------
-template <class Pol, int NP>
+template <class Pol, int NP, int RM>
 __device__ void wphase_true(const MemberDev<Pol> &M, const RowView<Pol> &v, typename Pol::comp eta, int j,
                             typename Pol::comp *wb, const WRow w, WFac<typename Pol::fac> &f,
                             typename Acc<Pol>::type (&part)[NP])
@@ -510,7 +587,7 @@ __device__ void wphase_true(const MemberDev<Pol> &M, const RowView<Pol> &v, type
     }
     part[0] += (typename Acc<Pol>::type)rr;
     part[1] += (typename Acc<Pol>::type)RR;
-    wstage0_finish(M, v, j, wb, w, f, staged);
+    wstage0_finish<Pol, RM>(M, v, j, wb, w, f, staged);
 }
 
 template <class Pol, int KM>
@@ -521,7 +598,7 @@ struct UbQuad {
     double ph4[4];
 };
 
-template <class Pol, int KM>
+template <class Pol, int KM, int RM>
 __device__ void wphase_ub(const MemberDev<Pol> &M, const MemberCtl &c, const RowView<Pol> &v,
                           typename Pol::comp eta, int j, typename Pol::comp *wb, const WRow w,
                           WFac<typename Pol::fac> &f, typename Acc<Pol>::type (&part)[2 + 2 * KM])
@@ -596,7 +673,7 @@ __device__ void wphase_ub(const MemberDev<Pol> &M, const MemberCtl &c, const Row
         stv4(v.r + i0, rs4);
     };
     quads<UbQuad<Pol, KM>>(nx, load, compute);
-    wstage0_finish(M, v, j, wb, w, f, staged);
+    wstage0_finish<Pol, RM>(M, v, j, wb, w, f, staged);
 }
 
 template <class Pol>
@@ -607,7 +684,7 @@ struct StQuad {
 
 // Richardson stage mu >= 1 (precond_stage): reads q_mu on rows j - 1 .. j + 1,
 // writes q_{mu+1} (the last stage writes e)
-template <class Pol>
+template <class Pol, int RM>
 __device__ void wprecond_stage(const MemberDev<Pol> &M, const RowView<Pol> &v, typename Pol::comp eta, int mu,
                                int j, typename Pol::comp *wb, const WRow w, WFac<typename Pol::fac> &f)
 {
@@ -655,7 +732,7 @@ __device__ void wprecond_stage(const MemberDev<Pol> &M, const RowView<Pol> &v, t
     quads<StQuad<Pol>>(nx, load, compute);
     __syncwarp();
     SW_TRACE(311);
-    if (opt3) wsolve_row(M, v, j, wb, w, f);
+    if (opt3) wsolve_row<Pol, RM>(M, v, j, wb, w, f);
     __syncwarp();
     SW_TRACE(312);
     wq_store_row(M, oh, of32, os, j, wb, w);
@@ -726,7 +803,7 @@ __device__ void wphase_le(const MemberDev<Pol> &M, const MemberCtl &c, const Row
 }
 
 // the first stage of option 3 from the stored r (phase_prec0)
-template <class Pol>
+template <class Pol, int RM>
 __device__ void wphase_prec0(const MemberDev<Pol> &M, const RowView<Pol> &v, typename Pol::comp eta, int j,
                              typename Pol::comp *wb, const WRow w, WFac<typename Pol::fac> &f)
 {
@@ -741,7 +818,7 @@ __device__ void wphase_prec0(const MemberDev<Pol> &M, const RowView<Pol> &v, typ
 #pragma unroll
         for (int u = 0; u < 4; ++u) wb[p0 + 33 * u] = stage0_input(M, v, eta, (comp)r4[u], i0 + u);
     }
-    wstage0_finish(M, v, j, wb, w, f, staged);
+    wstage0_finish<Pol, RM>(M, v, j, wb, w, f, staged);
 }
 
 // shared memory of one warp in the warp-per-row mode: its row buffer, then
