@@ -316,7 +316,7 @@ __device__ __forceinline__ void warp_affine_excl(T &a, T &b)
 // and with each lane walking its chunk of m points serially between two warp
 // scans.
 template <class T, class F>
-__device__ __forceinline__ void wtrisolve(T *wb, const WRow w, const F *lfT, const F *invDT, const F *__restrict__ zzT,
+__device__ __forceinline__ float wtrisolve(T *wb, const WRow w, const F *lfT, const F *invDT, const F *__restrict__ zzT,
                                        T gam, T ec, WFac<F> &f)
 {
     const int lane = threadIdx.x & 31, m = w.m;
@@ -376,15 +376,18 @@ __device__ __forceinline__ void wtrisolve(T *wb, const WRow w, const F *lfT, con
     wfac_wait(f);
 #pragma unroll 16
     for (int t = 0; t < m; ++t) col[t * 33] -= (T)zc[t * 32] * s;
+    return -1.f;
 }
 
 // The same solve with the lane's chunk of MM points and its multipliers held
 // in registers: the chunk, the multipliers, the inverse pivots and the
 // Sherman-Morrison vector are each read from shared memory once, and the
 // four walks run on registers.  Every value is computed by the same
-// expressions in the same order as in wtrisolve.
+// expressions in the same order as in wtrisolve.  Returns the largest
+// magnitude of the lane's results (FP32 rows; -1 for FP64) for the row
+// scale of the 16-bit store.
 template <class T, class F, int MM>
-__device__ __forceinline__ void wtrisolve_r(T *wb, const WRow w, const F *lfT, const F *invDT,
+__device__ __forceinline__ float wtrisolve_r(T *wb, const WRow w, const F *lfT, const F *invDT,
                                             const F *__restrict__ zzT, T gam, T ec, WFac<F> &f)
 {
     const int lane = threadIdx.x & 31;
@@ -440,16 +443,25 @@ __device__ __forceinline__ void wtrisolve_r(T *wb, const WRow w, const F *lfT, c
     const T yn = __shfl_sync(0xffffffffu, x[MM - 1], 31);
     const T s = gam * y0 + ec * yn;
     wfac_wait(f);
+    float mx = 0.f;
 #pragma unroll
-    for (int t = 0; t < MM; ++t) col[t * 33] = x[t] - (T)zc[t * 32] * s;
+    for (int t = 0; t < MM; ++t) {
+        const T r = x[t] - (T)zc[t * 32] * s;
+        col[t * 33] = r;
+        if constexpr (sizeof(T) == 4) mx = fmaxf(mx, fabsf(r));
+    }
+    return sizeof(T) == 4 ? mx : -1.f;
 }
 
 // store row j of a preconditioner field from the warp's buffer (q_store_row:
 // FP64; FP32 on the pole band; else 16-bit with a power-of-two row scale so
-// that the stored magnitudes are at most 1)
+// that the stored magnitudes are at most 1), with 16-byte stores.  lmax is
+// the lane's largest magnitude when the zonal solve left it (else negative:
+// it is taken from the buffer here); it is the same maximum over the same
+// values either way.
 template <class Pol>
 __device__ void wq_store_row(const MemberDev<Pol> &M, typename Pol::q16 *h, float *f32, float *sc, int j,
-                             const typename Pol::comp *wb, const WRow w)
+                             const typename Pol::comp *wb, const WRow w, float lmax)
 {
     typedef typename Pol::q16 qt;
     const int lane = threadIdx.x & 31, nx = w.nx;
@@ -459,21 +471,43 @@ __device__ void wq_store_row(const MemberDev<Pol> &M, typename Pol::q16 *h, floa
             *(double2 *)(h + row + i) = make_double2(wb[tpos(w, i)], wb[tpos(w, i + 1)]);
     } else {
         if (in_band(M, j)) {
-            for (int i = 2 * lane; i < nx; i += 64)
-                *(float2 *)(f32 + row + i) = make_float2(wb[tpos(w, i)], wb[tpos(w, i + 1)]);
+            for (int i = 4 * lane; i < nx; i += 128) {
+                const int p = tpos4(w, i);
+                *(float4 *)(f32 + row + i) = make_float4(wb[p], wb[p + 33], wb[p + 66], wb[p + 99]);
+            }
         } else {
-            float mx = 0.f;
-            for (int t = 0; t < w.m; ++t) mx = fmaxf(mx, fabsf(wb[t * 33 + lane]));
+            float mx = lmax;
+            if (mx < 0.f) {
+                mx = 0.f;
+                for (int t = 0; t < w.m; ++t) mx = fmaxf(mx, fabsf(wb[t * 33 + lane]));
+            }
             mx = warp_max(mx);
             float s = 1.f;
             if (mx > 0.f && mx <= 3.0e38f) { int e; frexpf(mx, &e); s = ldexpf(1.f, e); }
             else if (!(mx <= 3.0e38f)) s = mx;       // NaN / Inf: propagate
             const float inv = 1.f / s;                // exact: s is a power of two
-            for (int i = 2 * lane; i < nx; i += 64) {
-                qt q[2] = {f_to_q<qt>(wb[tpos(w, i)] * inv), f_to_q<qt>(wb[tpos(w, i + 1)] * inv)};
-                unsigned u;
-                memcpy(&u, q, sizeof(u));
-                *(unsigned *)(h + row + i) = u;
+            if (w.m >= 8) {
+                // 8 consecutive points per lane (their chunk positions are
+                // consecutive: i is a multiple of 8 and m of 8)
+                for (int i = 8 * lane; i < nx; i += 256) {
+                    const int p = tpos(w, i);
+                    qt q[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) q[u] = f_to_q<qt>(wb[p + 33 * u] * inv);
+                    uint4 v;
+                    memcpy(&v, q, sizeof(v));
+                    *(uint4 *)(h + row + i) = v;
+                }
+            } else {
+                for (int i = 4 * lane; i < nx; i += 128) {
+                    const int p = tpos4(w, i);
+                    qt q[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) q[u] = f_to_q<qt>(wb[p + 33 * u] * inv);
+                    uint2 v;
+                    memcpy(&v, q, sizeof(v));
+                    *(uint2 *)(h + row + i) = v;
+                }
             }
             if (lane == 0) sc[j] = s;
         }
@@ -483,7 +517,7 @@ __device__ void wq_store_row(const MemberDev<Pol> &M, typename Pol::q16 *h, floa
 // the zonal solve of row j (its factors staged by wfac_issue, or read from
 // global memory)
 template <class Pol, int RM>
-__device__ __forceinline__ void wsolve_row(const MemberDev<Pol> &M, const RowView<Pol> &v, int j,
+__device__ __forceinline__ float wsolve_row(const MemberDev<Pol> &M, const RowView<Pol> &v, int j,
                                            typename Pol::comp *wb, const WRow w, WFac<typename Pol::fac> &f)
 {
     typedef typename Pol::comp comp;
@@ -497,14 +531,14 @@ __device__ __forceinline__ void wsolve_row(const MemberDev<Pol> &M, const RowVie
     // chunks of up to RM FP32 points (RM / 4 FP64 points) in registers
     constexpr int rmax = sizeof(comp) == 4 ? RM : RM / 4;
     switch (w.m) {
-    case 4: if constexpr (rmax >= 4) { wtrisolve_r<comp, F, 4>(wb, w, lf, iD, M.zzT + row, gam, ec, f); return; } break;
-    case 8: if constexpr (rmax >= 8) { wtrisolve_r<comp, F, 8>(wb, w, lf, iD, M.zzT + row, gam, ec, f); return; } break;
-    case 16: if constexpr (rmax >= 16) { wtrisolve_r<comp, F, 16>(wb, w, lf, iD, M.zzT + row, gam, ec, f); return; } break;
-    case 32: if constexpr (rmax >= 32) { wtrisolve_r<comp, F, 32>(wb, w, lf, iD, M.zzT + row, gam, ec, f); return; } break;
-    case 64: if constexpr (rmax >= 64) { wtrisolve_r<comp, F, 64>(wb, w, lf, iD, M.zzT + row, gam, ec, f); return; } break;
+    case 4: if constexpr (rmax >= 4) return wtrisolve_r<comp, F, 4>(wb, w, lf, iD, M.zzT + row, gam, ec, f); break;
+    case 8: if constexpr (rmax >= 8) return wtrisolve_r<comp, F, 8>(wb, w, lf, iD, M.zzT + row, gam, ec, f); break;
+    case 16: if constexpr (rmax >= 16) return wtrisolve_r<comp, F, 16>(wb, w, lf, iD, M.zzT + row, gam, ec, f); break;
+    case 32: if constexpr (rmax >= 32) return wtrisolve_r<comp, F, 32>(wb, w, lf, iD, M.zzT + row, gam, ec, f); break;
+    case 64: if constexpr (rmax >= 64) return wtrisolve_r<comp, F, 64>(wb, w, lf, iD, M.zzT + row, gam, ec, f); break;
     default: break;
     }
-    wtrisolve<comp, F>(wb, w, lf, iD, M.zzT + row, gam, ec, f);
+    return wtrisolve<comp, F>(wb, w, lf, iD, M.zzT + row, gam, ec, f);
 }
 
 // the zonal solve (option 3) and the store of the first preconditioner stage
@@ -515,12 +549,13 @@ __device__ void wstage0_finish(const MemberDev<Pol> &M, const RowView<Pol> &v, i
 {
     __syncwarp();
     SW_TRACE(211);
-    if (M.pc >= 3) wsolve_row<Pol, RM>(M, v, j, wb, w, f);
+    float lmax = -1.f;
+    if (M.pc >= 3) lmax = wsolve_row<Pol, RM>(M, v, j, wb, w, f);
     else if (staged) wfac_wait(f);           // options 0-2: the copies still complete
     __syncwarp();
     SW_TRACE(212);
-    if (M.nstages == 1) wq_store_row(M, M.e, M.e32, M.e_s, j, wb, w);
-    else wq_store_row(M, M.qa, M.qa32, M.qa_s, j, wb, w);
+    if (M.nstages == 1) wq_store_row(M, M.e, M.e32, M.e_s, j, wb, w, lmax);
+    else wq_store_row(M, M.qa, M.qa32, M.qa_s, j, wb, w, lmax);
     __syncwarp();
     SW_TRACE(213);
 }
@@ -732,10 +767,11 @@ __device__ void wprecond_stage(const MemberDev<Pol> &M, const RowView<Pol> &v, t
     quads<StQuad<Pol>>(nx, load, compute);
     __syncwarp();
     SW_TRACE(311);
-    if (opt3) wsolve_row<Pol, RM>(M, v, j, wb, w, f);
+    float lmax = -1.f;
+    if (opt3) lmax = wsolve_row<Pol, RM>(M, v, j, wb, w, f);
     __syncwarp();
     SW_TRACE(312);
-    wq_store_row(M, oh, of32, os, j, wb, w);
+    wq_store_row(M, oh, of32, os, j, wb, w, lmax);
     __syncwarp();
     SW_TRACE(313);
 }
