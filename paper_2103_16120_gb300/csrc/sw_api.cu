@@ -619,6 +619,17 @@ static sw_status plan_launch(int n, const sw_grid *grids, const sw_solve_opts *o
                 P.grid = used;
             }
             P.warp = 1;
+            // every member with rows of 1024 or 2048 points (and GCR k <= 4,
+            // mixed precision, one block per SM): the kernel specialised for
+            // that row length, with one zonal-solve variant compiled in
+            const int m0 = grids[0]->nx / 32;
+            bool one_len = P.minb == 1 && o->k <= 4 && o->prec != SW_PREC_FP64 && (m0 == 32 || m0 == 64);
+            for (int m = 1; m < n && one_len; ++m) one_len = grids[m]->nx == grids[0]->nx;
+            if (one_len) {
+                int bs = 0;
+                CK(gcr_occupancy(o->prec, o->k, 1, m0, P.threads, P.smem, &bs));
+                if (bs >= bps) P.warp = m0;
+            }
         } else if (o->row_mode == 2) {
             return fail(SW_ERR_INVALID_ARG, "row_mode 2: the warp-per-row kernel does not fit this device");
         } else {
@@ -663,7 +674,7 @@ static void fill_desc(EnsDesc &D, int n, const sw_grid *grids, const Plan &P, sw
     D.grid = P.grid;
     D.cache_const = P.cc;
     D.cache_state = P.cs;
-    D.warp_rows = P.warp;
+    D.warp_rows = P.warp != 0;
     D.warp_stage = P.stage;
     D.cta_begin[0] = 0;
     for (int m = 0; m < n; ++m) {
@@ -733,7 +744,7 @@ static sw_status solve_one_async(sw_grid g, const sw_solve_opts *o, const double
     a.nb0 = P.nb[0];
     a.cache_const = P.cc;
     a.cache_state = P.cs;
-    a.warp_rows = P.warp;
+    a.warp_rows = P.warp != 0;
     a.warp_stage = P.stage;
     CK(launch_init_one(a, s));
     CK(launch_gcr(o->prec, o->k, P.minb, P.warp, g->desc, P.grid, max_nx, P.threads, P.smem, s));

@@ -615,7 +615,7 @@ __device__ void advance(const MemberDev<Pol> &M, MemberCtl &c, const double *tot
 // per SM the register allocation is made for (2 for grids whose blocks own
 // several rows each: twice the warps to overlap their memory latency, at the
 // price of a few spilled registers)
-template <class Pol, int KM, int MINB, bool WARP>
+template <class Pol, int KM, int MINB, int WARP>
 __global__ void __launch_bounds__(MAX_THREADS, MINB) k_gcr(const EnsDesc *__restrict__ D, int max_nx)
 {
     typedef typename Pol::comp comp;
@@ -651,10 +651,14 @@ __global__ void __launch_bounds__(MAX_THREADS, MINB) k_gcr(const EnsDesc *__rest
     const int ny = M.ny, nx = M.nx;
     unsigned char *ws = dsm;
     // warp mode: the warps' row buffers, then the reduction scratch
-    constexpr bool wmode = WARP;          // one warp per row (D->warp_rows)
-    // longest zonal-solve chunk (FP32 points per lane) kept in registers: 64
-    // with the register budget of one block per SM, 16 with that of two
-    constexpr int RM = MINB == 1 ? 64 : 16;
+    // WARP: 0 one block per row; 1 one warp per row (D->warp_rows), rows of
+    // any length; m > 1 one warp per row, specialised for rows of 32 m points
+    // (only that zonal-solve variant is compiled in: a smaller kernel)
+    constexpr bool wmode = WARP != 0;
+    // the zonal solve's register chunks: exactly WARP points, or up to 64
+    // FP32 points with the register budget of one block per SM, 16 with that
+    // of two
+    constexpr int SEL = WARP > 1 ? WARP : (MINB == 1 ? -64 : -16);
     const WRow wr = wrow(nx);
     double *scratch;
     typedef typename Pol::fac fac_t;
@@ -722,15 +726,15 @@ __global__ void __launch_bounds__(MAX_THREADS, MINB) k_gcr(const EnsDesc *__rest
                             const SplitState S = {M.shat, M.sdx, M.scx, M.sdy, M.scy};
                             split_true_row<Pol, NP>(M, S, v, eta, j, threadIdx.x & 31, 32, part,
                                                     [&](int i, comp x) { wb[tpos(wr, i)] = x; });
-                            wstage0_finish<Pol, RM>(M, v, j, wb, wr, wf, staged);
+                            wstage0_finish<Pol, SEL>(M, v, j, wb, wr, wf, staged);
                             break;
                         }
                     }
-                    wphase_true<Pol, NP, RM>(M, v, eta, j, wb, wr, wf, part);
+                    wphase_true<Pol, NP, SEL>(M, v, eta, j, wb, wr, wf, part);
                     break;
-                case PH_UB: wphase_ub<Pol, KM, RM>(M, s_c, v, eta, j, wb, wr, wf, part); break;
-                case PH_PREC: wprecond_stage<Pol, RM>(M, v, eta, s_c.stage, j, wb, wr, wf); break;
-                case PH_PREC0: wphase_prec0<Pol, RM>(M, v, eta, j, wb, wr, wf); break;
+                case PH_UB: wphase_ub<Pol, KM, SEL>(M, s_c, v, eta, j, wb, wr, wf, part); break;
+                case PH_PREC: wprecond_stage<Pol, SEL>(M, v, eta, s_c.stage, j, wb, wr, wf); break;
+                case PH_PREC0: wphase_prec0<Pol, SEL>(M, v, eta, j, wb, wr, wf); break;
                 case PH_LE: wphase_le<Pol, KM>(M, s_c, v, j, wr, part); break;
                 case PH_ZERO:
                     for (int i = threadIdx.x & 31; i < nx; i += 32) M.phi[(size_t)j * nx + i] = 0.0;
@@ -928,12 +932,7 @@ __global__ void __launch_bounds__(MAX_THREADS, MINB) k_gcr(const EnsDesc *__rest
 #define SW_GCR_TRACE_FN(TAG)
 #endif
 
-#define SW_GCR_UNIT(POL, WARP, TAG)                                                               \
-    const void *gcr_kernel_##TAG(int k, int minb)                                                 \
-    {                                                                                             \
-        if (k <= 4) return minb > 1 ? (const void *)k_gcr<POL, 4, 2, WARP> : (const void *)k_gcr<POL, 4, 1, WARP>; \
-        return minb > 1 ? (const void *)k_gcr<POL, KMAX, 2, WARP> : (const void *)k_gcr<POL, KMAX, 1, WARP>;     \
-    }                                                                                             \
+#define SW_GCR_DEBUG_FN(TAG)                                                                      \
     cudaError_t gcr_debug_##TAG(unsigned long long extra, unsigned long long limit_ns)            \
     {                                                                                             \
         cudaError_t e = cudaMemcpyToSymbol(g_extra_arrivals, &extra, sizeof(extra));              \
@@ -941,5 +940,24 @@ __global__ void __launch_bounds__(MAX_THREADS, MINB) k_gcr(const EnsDesc *__rest
         return e;                                                                                 \
     }                                                                                             \
     SW_GCR_TRACE_FN(TAG)
+
+#define SW_GCR_UNIT(POL, WARP, TAG)                                                               \
+    const void *gcr_kernel_##TAG(int k, int minb)                                                 \
+    {                                                                                             \
+        if (k <= 4) return minb > 1 ? (const void *)k_gcr<POL, 4, 2, WARP> : (const void *)k_gcr<POL, 4, 1, WARP>; \
+        return minb > 1 ? (const void *)k_gcr<POL, KMAX, 2, WARP> : (const void *)k_gcr<POL, KMAX, 1, WARP>;     \
+    }                                                                                             \
+    SW_GCR_DEBUG_FN(TAG)
+
+// the warp-per-row kernels specialised for one row length (chunks of 32 or 64
+// points per lane), GCR k <= 4 and one block per SM
+#define SW_GCR_SPEC_UNIT(POL, TAG)                                                                \
+    const void *gcr_kernel_##TAG(int m)                                                           \
+    {                                                                                             \
+        if (m == 64) return (const void *)k_gcr<POL, 4, 1, 64>;                                   \
+        if (m == 32) return (const void *)k_gcr<POL, 4, 1, 32>;                                   \
+        return nullptr;                                                                           \
+    }                                                                                             \
+    SW_GCR_DEBUG_FN(TAG)
 
 } // namespace sw

@@ -2,5 +2,5 @@
 #include "sw_gcr.cuh"
 
 namespace sw {
-SW_GCR_UNIT(PolBF16, false, bf16)
+SW_GCR_UNIT(PolBF16, 0, bf16)
 } // namespace sw

@@ -2,5 +2,5 @@
 #include "sw_gcr.cuh"
 
 namespace sw {
-SW_GCR_UNIT(PolF16, false, f16)
+SW_GCR_UNIT(PolF16, 0, f16)
 } // namespace sw

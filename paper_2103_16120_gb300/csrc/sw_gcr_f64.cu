@@ -2,5 +2,5 @@
 #include "sw_gcr.cuh"
 
 namespace sw {
-SW_GCR_UNIT(PolFP64, false, f64)
+SW_GCR_UNIT(PolFP64, 0, f64)
 } // namespace sw

@@ -2,5 +2,5 @@
 #include "sw_gcr.cuh"
 
 namespace sw {
-SW_GCR_UNIT(PolF16, true, w16)
+SW_GCR_UNIT(PolF16, 1, w16)
 } // namespace sw

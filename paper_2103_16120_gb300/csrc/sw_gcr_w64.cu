@@ -2,5 +2,5 @@
 #include "sw_gcr.cuh"
 
 namespace sw {
-SW_GCR_UNIT(PolFP64, true, w64)
+SW_GCR_UNIT(PolFP64, 1, w64)
 } // namespace sw

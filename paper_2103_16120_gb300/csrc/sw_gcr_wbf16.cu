@@ -2,5 +2,5 @@
 #include "sw_gcr.cuh"
 
 namespace sw {
-SW_GCR_UNIT(PolBF16, true, wbf16)
+SW_GCR_UNIT(PolBF16, 1, wbf16)
 } // namespace sw

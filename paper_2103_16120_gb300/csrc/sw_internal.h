@@ -88,6 +88,14 @@ SW_GCR_UNIT_DECL(w64)
 SW_GCR_UNIT_DECL(w16)
 SW_GCR_UNIT_DECL(wbf16)
 SW_GCR_UNIT_DECL(solver)
+// the warp-per-row kernels specialised for rows of 32 m points (m = 32, 64;
+// GCR k <= 4, one block per SM; null for other m)
+const void *gcr_kernel_s16(int m);
+const void *gcr_kernel_sbf16(int m);
+cudaError_t gcr_debug_s16(unsigned long long extra, unsigned long long limit_ns);
+cudaError_t gcr_debug_sbf16(unsigned long long extra, unsigned long long limit_ns);
+void gcr_trace_s16(unsigned long long *buf, int cap, int block);
+void gcr_trace_sbf16(unsigned long long *buf, int cap, int block);
 cudaError_t launch_operator_f64(const OpArgs<double> &a, const double *x, double *y, int threads, cudaStream_t s);
 cudaError_t launch_operator_f32(const OpArgs<float> &a, const float *x, float *y, int threads, cudaStream_t s);
 cudaError_t launch_precond(int prec, const void *Mdev, int nx, int ny, int nstages, void *qout, int threads,

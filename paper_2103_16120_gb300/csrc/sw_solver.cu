@@ -266,9 +266,14 @@ size_t gcr_smem_bytes(int prec, int max_nx, int k, int cache_const, int cache_st
 }
 
 // the instantiation of k_gcr for a precision, a GCR k, the register budget and
-// the row mode
+// the row mode (warp 0: block per row; 1: warp per row; m > 1: warp per row,
+// specialised for rows of 32 m points)
 static const void *gcr_kernel(int prec, int k, int minb, int warp)
 {
+    if (warp > 1) {
+        if (k > 4 || minb != 1) return nullptr;
+        return prec == 1 ? gcr_kernel_s16(warp) : (prec == 2 ? gcr_kernel_sbf16(warp) : nullptr);
+    }
     switch (prec) {
     case 0: return warp ? gcr_kernel_w64(k, minb) : gcr_kernel_f64(k, minb);
     case 1: return warp ? gcr_kernel_w16(k, minb) : gcr_kernel_f16(k, minb);
@@ -445,6 +450,7 @@ extern "C" void sw_trace_configure(unsigned long long *buf, int cap, int block)
     gcr_trace_solver(buf, cap, block);
     gcr_trace_f64(buf, cap, block); gcr_trace_f16(buf, cap, block); gcr_trace_bf16(buf, cap, block);
     gcr_trace_w64(buf, cap, block); gcr_trace_w16(buf, cap, block); gcr_trace_wbf16(buf, cap, block);
+    gcr_trace_s16(buf, cap, block); gcr_trace_sbf16(buf, cap, block);
 }
 #endif
 
@@ -452,7 +458,8 @@ extern "C" void sw_trace_configure(unsigned long long *buf, int cap, int block)
 cudaError_t set_barrier_debug(unsigned long long extra, unsigned long long limit_ns)
 {
     cudaError_t (*const set[])(unsigned long long, unsigned long long) = {
-        gcr_debug_f64, gcr_debug_f16, gcr_debug_bf16, gcr_debug_w64, gcr_debug_w16, gcr_debug_wbf16};
+        gcr_debug_f64, gcr_debug_f16, gcr_debug_bf16, gcr_debug_w64, gcr_debug_w16, gcr_debug_wbf16,
+        gcr_debug_s16, gcr_debug_sbf16};
     for (auto f : set) {
         cudaError_t e = f(extra, limit_ns);
         if (e != cudaSuccess) return e;

@@ -516,7 +516,7 @@ __device__ void wq_store_row(const MemberDev<Pol> &M, typename Pol::q16 *h, floa
 
 // the zonal solve of row j (its factors staged by wfac_issue, or read from
 // global memory)
-template <class Pol, int RM>
+template <class Pol, int SEL>
 __device__ __forceinline__ float wsolve_row(const MemberDev<Pol> &M, const RowView<Pol> &v, int j,
                                            typename Pol::comp *wb, const WRow w, WFac<typename Pol::fac> &f)
 {
@@ -528,8 +528,15 @@ __device__ __forceinline__ float wsolve_row(const MemberDev<Pol> &M, const RowVi
     const F *lf = f.lf ? (const F *)f.lf : M.lfT + row;
     const F *iD = f.lf ? (const F *)f.iD : M.invDT + row;
     const comp gam = (comp)v.gam, ec = (comp)v.ec;
-    // chunks of up to RM FP32 points (RM / 4 FP64 points) in registers
-    constexpr int rmax = sizeof(comp) == 4 ? RM : RM / 4;
+    // SEL > 0: the kernel is specialised for rows whose chunk is SEL points
+    // (its only register variant); SEL < 0: chunks of up to -SEL FP32 points
+    // (-SEL / 4 FP64 points) in registers.  Other rows take the walks over
+    // shared memory.
+    if constexpr (SEL > 0) {
+        if (w.m == SEL) return wtrisolve_r<comp, F, SEL>(wb, w, lf, iD, M.zzT + row, gam, ec, f);
+        return wtrisolve<comp, F>(wb, w, lf, iD, M.zzT + row, gam, ec, f);
+    }
+    constexpr int rmax = SEL > 0 ? 0 : (sizeof(comp) == 4 ? -SEL : -SEL / 4);
     switch (w.m) {
     case 4: if constexpr (rmax >= 4) return wtrisolve_r<comp, F, 4>(wb, w, lf, iD, M.zzT + row, gam, ec, f); break;
     case 8: if constexpr (rmax >= 8) return wtrisolve_r<comp, F, 8>(wb, w, lf, iD, M.zzT + row, gam, ec, f); break;
@@ -543,14 +550,14 @@ __device__ __forceinline__ float wsolve_row(const MemberDev<Pol> &M, const RowVi
 
 // the zonal solve (option 3) and the store of the first preconditioner stage
 // of row j, whose input the warp's buffer holds (stage0_finish)
-template <class Pol, int RM>
+template <class Pol, int SEL>
 __device__ void wstage0_finish(const MemberDev<Pol> &M, const RowView<Pol> &v, int j, typename Pol::comp *wb,
                                const WRow w, WFac<typename Pol::fac> &f, bool staged)
 {
     __syncwarp();
     SW_TRACE(211);
     float lmax = -1.f;
-    if (M.pc >= 3) lmax = wsolve_row<Pol, RM>(M, v, j, wb, w, f);
+    if (M.pc >= 3) lmax = wsolve_row<Pol, SEL>(M, v, j, wb, w, f);
     else if (staged) wfac_wait(f);           // options 0-2: the copies still complete
     __syncwarp();
     SW_TRACE(212);
@@ -577,7 +584,7 @@ __device__ __forceinline__ void quads(int nx, LD load, CP compute)
 // phases on one row j (one warp); the thread adds its share of the phase's
 // inner products to part (phase_true, phase_ub, precond_stage, phase_le)
 // ---------------------------------------------------------------------------
-template <class Pol, int NP, int RM>
+template <class Pol, int NP, int SEL>
 __device__ void wphase_true(const MemberDev<Pol> &M, const RowView<Pol> &v, typename Pol::comp eta, int j,
                             typename Pol::comp *wb, const WRow w, WFac<typename Pol::fac> &f,
                             typename Acc<Pol>::type (&part)[NP])
@@ -622,7 +629,7 @@ __device__ void wphase_true(const MemberDev<Pol> &M, const RowView<Pol> &v, type
     }
     part[0] += (typename Acc<Pol>::type)rr;
     part[1] += (typename Acc<Pol>::type)RR;
-    wstage0_finish<Pol, RM>(M, v, j, wb, w, f, staged);
+    wstage0_finish<Pol, SEL>(M, v, j, wb, w, f, staged);
 }
 
 template <class Pol, int KM>
@@ -633,7 +640,7 @@ struct UbQuad {
     double ph4[4];
 };
 
-template <class Pol, int KM, int RM>
+template <class Pol, int KM, int SEL>
 __device__ void wphase_ub(const MemberDev<Pol> &M, const MemberCtl &c, const RowView<Pol> &v,
                           typename Pol::comp eta, int j, typename Pol::comp *wb, const WRow w,
                           WFac<typename Pol::fac> &f, typename Acc<Pol>::type (&part)[2 + 2 * KM])
@@ -708,7 +715,7 @@ __device__ void wphase_ub(const MemberDev<Pol> &M, const MemberCtl &c, const Row
         stv4(v.r + i0, rs4);
     };
     quads<UbQuad<Pol, KM>>(nx, load, compute);
-    wstage0_finish<Pol, RM>(M, v, j, wb, w, f, staged);
+    wstage0_finish<Pol, SEL>(M, v, j, wb, w, f, staged);
 }
 
 template <class Pol>
@@ -719,7 +726,7 @@ struct StQuad {
 
 // Richardson stage mu >= 1 (precond_stage): reads q_mu on rows j - 1 .. j + 1,
 // writes q_{mu+1} (the last stage writes e)
-template <class Pol, int RM>
+template <class Pol, int SEL>
 __device__ void wprecond_stage(const MemberDev<Pol> &M, const RowView<Pol> &v, typename Pol::comp eta, int mu,
                                int j, typename Pol::comp *wb, const WRow w, WFac<typename Pol::fac> &f)
 {
@@ -768,7 +775,7 @@ __device__ void wprecond_stage(const MemberDev<Pol> &M, const RowView<Pol> &v, t
     __syncwarp();
     SW_TRACE(311);
     float lmax = -1.f;
-    if (opt3) lmax = wsolve_row<Pol, RM>(M, v, j, wb, w, f);
+    if (opt3) lmax = wsolve_row<Pol, SEL>(M, v, j, wb, w, f);
     __syncwarp();
     SW_TRACE(312);
     wq_store_row(M, oh, of32, os, j, wb, w, lmax);
@@ -839,7 +846,7 @@ __device__ void wphase_le(const MemberDev<Pol> &M, const MemberCtl &c, const Row
 }
 
 // the first stage of option 3 from the stored r (phase_prec0)
-template <class Pol, int RM>
+template <class Pol, int SEL>
 __device__ void wphase_prec0(const MemberDev<Pol> &M, const RowView<Pol> &v, typename Pol::comp eta, int j,
                              typename Pol::comp *wb, const WRow w, WFac<typename Pol::fac> &f)
 {
@@ -854,7 +861,7 @@ __device__ void wphase_prec0(const MemberDev<Pol> &M, const RowView<Pol> &v, typ
 #pragma unroll
         for (int u = 0; u < 4; ++u) wb[p0 + 33 * u] = stage0_input(M, v, eta, (comp)r4[u], i0 + u);
     }
-    wstage0_finish<Pol, RM>(M, v, j, wb, w, f, staged);
+    wstage0_finish<Pol, SEL>(M, v, j, wb, w, f, staged);
 }
 
 // shared memory of one warp in the warp-per-row mode: its row buffer, then
