@@ -73,7 +73,7 @@ SEQS = {
 # mixed-precision solver kernel per launch (seq512) or per GCR iteration
 # (seq2048, scaled by the launch's iterations); None until captured for the
 # current kernel
-TRAFFIC = {"seq512": None, "seq2048_per_iteration": 71.92e9 / 275}
+TRAFFIC = {"seq512": None, "seq2048_per_iteration": 71.82e9 / 275}
 
 
 def dist_env():
@@ -549,7 +549,8 @@ def run_gpu(args):
             "solution_rel_error_vs_fp64_oracle": err,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "k_gcr<PolF16> (persistent GCR)",
+                         "kernel": ("k_gcr<PolF16> (persistent GCR, one warp per row, specialised for rows of 2048 points)"
+                                    if wl == "seq2048" else "k_gcr<PolF16> (persistent GCR)"),
                          "kernel_ms_per_launch": kms, "kernel_mean_iterations": kits,
                          "algorithmic_bytes_per_point": bpp, "note": note,
                          "peak_source": "measured hbm_gbs (of measured)" if peaks else "fallback 6800 GB/s"},
