@@ -12,17 +12,12 @@ preconditioner, higher precision at the poles and in the residual update):
 
   field                                   stored as
   r, p_l, L(p_l), L(e)                    FP32
-  the solver's increments Delta Phi       FP32 (Sec. 4.3: the increments
-                                          are accumulated in single precision
-                                          and added to Phi when the solver
-                                          exits; here also at every true
-                                          residual, the reliable update)
   preconditioner stages q_mu and e        FP16 (or BF16) after division by a
                                           power-of-two row scale; FP32 on the
                                           pole-band rows
   coefficients of L and of T              FP32 (used by P^-1 and L(e))
   Phi, inner products, alpha, beta,       FP64
-  true residual L(Phi + Delta Phi) - R
+  true residual L(Phi) - R
 
 The row scale is not in the paper: an IEEE half has 5 exponent bits where the
 paper's emulated half keeps 11 (Sec. 4.1), so each 16-bit row is stored as
@@ -153,20 +148,17 @@ class MixedSolve:
         r = store(rt, vf)
         p = [self.precond(r, opts, eta)]
         Lp = [store(W.operator(p[0]), vf)]
-        dphi = np.zeros_like(R)                           # increments since the last fold
         it = nu = 0
         while True:
-            # step 2: beta minimises ||r + beta L p_nu||; the increment goes
-            # into Delta Phi (vector format), Phi itself changes at the folds
+            # step 2: beta minimises ||r + beta L p_nu||
             beta = -np.sum(r * Lp[nu]) / np.sum(Lp[nu] * Lp[nu])
-            dphi = store(dphi + beta * p[nu], vf)
+            phi = phi + beta * p[nu]
             r = store(r + beta * Lp[nu], vf)
             it += 1
             rn = float(np.sqrt(np.sum(r * r)))
             if (rn <= tol * nR and it >= opts.min_iters) or it >= opts.max_iters or \
                (opts.ru_every > 0 and it % opts.ru_every == 0):
-                rt = E.operator(phi + dphi) - R
-                phi, dphi = phi + dphi, np.zeros_like(R)  # fold the increments into Phi
+                rt = E.operator(phi) - R
                 rn = float(np.sqrt(np.sum(rt * rt)))
                 st["true_rel_residual"] = rn / nR
                 if rn <= tol * nR and it >= opts.min_iters:
