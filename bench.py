@@ -427,25 +427,55 @@ def run_gpu(args):
     kms, kits = solver_only(mixed, min(args.steps, 50 if wl == "seq512" else 8))
 
     # --- end to end through host buffers ----------------------------------
+    # every step copies its coefficients and R from pinned host memory and
+    # reads its solution back; the copies of step s + 1 run on a copy stream
+    # into the second of two device buffer sets while step s solves
     n_host = min(nsets, 50 if wl == "seq512" else 4)
     hcoef = [[torch.as_tensor(P[k]).pin_memory() for k in KEYS] for P in seq[:n_host]]
     hR = [torch.as_tensor(P["R"]).pin_memory() for P in seq[:n_host]]
     hphi = torch.zeros((ny, nx), dtype=torch.float64).pin_memory()
-    dco = [torch.empty((ny, nx), dtype=torch.float64, device=dev) for _ in KEYS]
-    dR = torch.empty((ny, nx), dtype=torch.float64, device=dev)
+    dco = [[torch.empty((ny, nx), dtype=torch.float64, device=dev) for _ in KEYS] for _ in range(2)]
+    dR = [torch.empty((ny, nx), dtype=torch.float64, device=dev) for _ in range(2)]
     dphi = torch.zeros((ny, nx), dtype=torch.float64, device=dev)
     n_e2e = min(args.steps, 50 if wl == "seq512" else 10)
     ebuf = sw.stats_buffer(max(n_e2e, 3))
+    cstream = torch.cuda.Stream(device=dev)
+    ready = [torch.cuda.Event(), torch.cuda.Event()]
+    free = [torch.cuda.Event(), torch.cuda.Event()]
+    # the solution read back through a device copy, also on the copy stream
+    dout = [torch.empty((ny, nx), dtype=torch.float64, device=dev) for _ in range(2)]
+    solved = [torch.cuda.Event(), torch.cuda.Event()]
+    read = [torch.cuda.Event(), torch.cuda.Event()]
+
+    def h2d(s_):
+        b, t = s_ % 2, s_ % len(hR)
+        with torch.cuda.stream(cstream):
+            cstream.wait_event(free[b])          # the solve that last read buffer set b is done
+            for d, h in zip(dco[b], hcoef[t]):
+                d.copy_(h, non_blocking=True)
+            dR[b].copy_(hR[t], non_blocking=True)
+            ready[b].record(cstream)
 
     def e2e_steps(n):
+        for b in range(2):
+            free[b].record(stream)
+            read[b].record(stream)
+        h2d(0)
         for s_ in range(n):
-            t = s_ % len(hR)
-            for d, h in zip(dco, hcoef[t]):
-                d.copy_(h, non_blocking=True)
-            dR.copy_(hR[t], non_blocking=True)
-            sw.sw_elliptic_set_coeffs(g, *dco)
-            sw.sw_ensemble_solve_async([g], mixed, [dR], [dphi], ebuf[s_ * stat_bytes:(s_ + 1) * stat_bytes])
-            hphi.copy_(dphi, non_blocking=True)
+            b = s_ % 2
+            if s_ + 1 < n:
+                h2d(s_ + 1)
+            stream.wait_event(ready[b])
+            sw.sw_elliptic_set_coeffs(g, *dco[b])
+            sw.sw_ensemble_solve_async([g], mixed, [dR[b]], [dphi], ebuf[s_ * stat_bytes:(s_ + 1) * stat_bytes])
+            free[b].record(stream)
+            stream.wait_event(read[b])              # the read-back that last used dout[b] is done
+            dout[b].copy_(dphi)
+            solved[b].record(stream)
+            with torch.cuda.stream(cstream):
+                cstream.wait_event(solved[b])
+                hphi.copy_(dout[b], non_blocking=True)
+                read[b].record(cstream)
         torch.cuda.synchronize()
         checked(ebuf, n)
 

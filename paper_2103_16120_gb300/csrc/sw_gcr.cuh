@@ -662,7 +662,7 @@ __global__ void __launch_bounds__(MAX_THREADS, MINB) k_gcr(const EnsDesc *__rest
     const WRow wr = wrow(nx);
     double *scratch;
     typedef typename Pol::fac fac_t;
-    WFac<fac_t> wf = {nullptr, nullptr, 0u, 0u, &B->g.abort};
+    WFac<fac_t> wf = {nullptr, nullptr, 0u, 0u, &B->g.abort, -1};
     comp *wb = nullptr;
     if constexpr (wmode) {
         // per warp: row buffer, staged factor rows, mbarrier (warp_slot_bytes)
@@ -722,7 +722,7 @@ __global__ void __launch_bounds__(MAX_THREADS, MINB) k_gcr(const EnsDesc *__rest
                         if (M.split && s_c.init) {
                             // the initial residual by Eq. 14 (split fluid thickness)
                             const bool staged = wf.lf && M.pc >= 3;
-                            if (staged) wfac_issue(wf, M.lfT + (size_t)j * nx, M.invDT + (size_t)j * nx, nx);
+                            if (staged) wfac_issue(wf, j, M.lfT + (size_t)j * nx, M.invDT + (size_t)j * nx, nx);
                             const SplitState S = {M.shat, M.sdx, M.scx, M.sdy, M.scy};
                             split_true_row<Pol, NP>(M, S, v, eta, j, threadIdx.x & 31, 32, part,
                                                     [&](int i, comp x) { wb[tpos(wr, i)] = x; });
@@ -741,6 +741,17 @@ __global__ void __launch_bounds__(MAX_THREADS, MINB) k_gcr(const EnsDesc *__rest
                     break;
                 default: break;
                 }
+            }
+            // the factors of the warp's first row for the next phase's zonal
+            // solve, started now so that the copies overlap the member
+            // barrier: a solve follows L(e) (the update), the update or the
+            // true residual or an earlier stage (a Richardson stage)
+            if (wf.lf && M.pc >= 3) {
+                const int jf = wi * nb + local, ph = s_c.phase;
+                const bool next_solves = ph == PH_LE ||
+                                         ((ph == PH_UB || ph == PH_TRUE || ph == PH_PREC0) && M.nstages > 1) ||
+                                         (ph == PH_PREC && s_c.stage + 1 < M.nstages);
+                if (jf < ny && next_solves) wfac_ahead(wf, jf, M.lfT + (size_t)jf * nx, M.invDT + (size_t)jf * nx, nx);
             }
             __syncthreads();
         } else {
@@ -884,6 +895,10 @@ __global__ void __launch_bounds__(MAX_THREADS, MINB) k_gcr(const EnsDesc *__rest
             S.eta = *M.etap;
             D->stats[m] = S;
         }
+    }
+    // copies started ahead for a phase that did not come (the solve ended)
+    if constexpr (wmode) {
+        if (wf.pre >= 0) wfac_wait(wf);
     }
     // per-row norms of the final true residual
     const bool want_rowres = ok && s_c.phase == PH_DONE && M.rowres && (s_c.status == ST_OK || s_c.status == ST_NOT_CONVERGED);

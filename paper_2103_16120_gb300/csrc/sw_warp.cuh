@@ -222,6 +222,7 @@ struct WFac {
     unsigned bar;          // shared address of the warp's mbarrier
     unsigned parity;       // phase parity of the next wait
     int *abort;            // the member's abort flag, set when a wait runs out
+    int pre;               // row whose lf and invD copies were started ahead (else -1)
 };
 
 // lane 0 starts the copy of one or two rows (src1 optional) into the warp's
@@ -244,11 +245,25 @@ __device__ __forceinline__ void wfac_copy(const WFac<F> &f, F *dst0, const F *sr
     }
 }
 
-// the row's multipliers and inverse pivots, when its phase begins
+// the multipliers and inverse pivots of row j, when its phase begins (unless
+// they were started ahead, across the member barrier: wfac_ahead)
 template <class F>
-__device__ __forceinline__ void wfac_issue(const WFac<F> &f, const F *lfT, const F *iDT, int nx)
+__device__ __forceinline__ void wfac_issue(WFac<F> &f, int j, const F *lfT, const F *iDT, int nx)
 {
-    if (f.lf) wfac_copy(f, f.lf, lfT, f.iD, iDT, nx);
+    if (!f.lf) return;
+    if (f.pre == j) { f.pre = -1; return; }
+    wfac_copy(f, f.lf, lfT, f.iD, iDT, nx);
+}
+
+// start the copies of row j's factors for the next phase now, so that they
+// overlap the member barrier (the buffers are free at the end of a phase's
+// rows; the factors are read-only)
+template <class F>
+__device__ __forceinline__ void wfac_ahead(WFac<F> &f, int j, const F *lfT, const F *iDT, int nx)
+{
+    if (!f.lf || f.pre >= 0) return;
+    wfac_copy(f, f.lf, lfT, f.iD, iDT, nx);
+    f.pre = j;
 }
 
 __device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity)
@@ -593,7 +608,7 @@ __device__ void wphase_true(const MemberDev<Pol> &M, const RowView<Pol> &v, type
     const int nx = M.nx, ny = M.ny, lane = threadIdx.x & 31;
     const size_t row = (size_t)j * nx, rs = j > 0 ? row - nx : row;
     const bool staged = f.lf && M.pc >= 3;
-    if (staged) wfac_issue(f, M.lfT + row, M.invDT + row, nx);
+    if (staged) wfac_issue(f, j, M.lfT + row, M.invDT + row, nx);
     const RowCoef<double> c = {M.ax + row, M.cx + row, M.bx + row, M.ay + row, M.cy + row, M.by + row,
                                M.ay + rs, M.cy + rs, M.by + rs, M.C + row};
     int srcS, shS, srcN, shN;
@@ -651,7 +666,7 @@ __device__ void wphase_ub(const MemberDev<Pol> &M, const MemberCtl &c, const Row
     const int nx = M.nx;
     const size_t row = (size_t)j * nx;
     const bool staged = f.lf && M.pc >= 3;
-    if (staged) wfac_issue(f, M.lfT + row, M.invDT + row, nx);
+    if (staged) wfac_issue(f, j, M.lfT + row, M.invDT + row, nx);
     const int nd = c.nu + 1;                      // directions before the new one
     vec *pn = v.pb + (size_t)phys_slot(c, M.k, nd) * v.vstride;
     vec *Lpn = v.Lpb + (size_t)phys_slot(c, M.k, nd) * v.vstride;
@@ -736,7 +751,7 @@ __device__ void wprecond_stage(const MemberDev<Pol> &M, const RowView<Pol> &v, t
     const size_t row = (size_t)j * nx;
     const bool opt3 = (M.pc >= 3), has_n = j < ny - 1, has_s = j > 0;
     const bool staged = f.lf && opt3;
-    if (staged) wfac_issue(f, M.lfT + row, M.invDT + row, nx);
+    if (staged) wfac_issue(f, j, M.lfT + row, M.invDT + row, nx);
     const bool last = (mu == M.nstages - 1);
     const typename Pol::q16 *ih = (mu & 1) ? M.qa : M.qb;
     const float *if32 = (mu & 1) ? M.qa32 : M.qb32;
@@ -853,7 +868,7 @@ __device__ void wphase_prec0(const MemberDev<Pol> &M, const RowView<Pol> &v, typ
     typedef typename Pol::comp comp;
     const int lane = threadIdx.x & 31;
     const bool staged = f.lf && M.pc >= 3;
-    if (staged) wfac_issue(f, M.lfT + (size_t)j * M.nx, M.invDT + (size_t)j * M.nx, M.nx);
+    if (staged) wfac_issue(f, j, M.lfT + (size_t)j * M.nx, M.invDT + (size_t)j * M.nx, M.nx);
     for (int i0 = 4 * lane; i0 < M.nx; i0 += 128) {
         typename Pol::res r4[4];
         ldv4(v.r + i0, r4);
