@@ -73,7 +73,13 @@ typedef enum {
                                    directions alternate between option 3 and
                                    a sw_model's network (opts.model), e = s y / d;
                                    a network direction that does not help is
-                                   replaced by option 3 */
+                                   replaced by option 3.  The network turns of
+                                   a single-grid solve run on the device, in a
+                                   CUDA graph with a conditional node that the
+                                   grid builds once per configuration (and
+                                   rebuilds when the grid's workspace, the
+                                   model's activations or the launch change),
+                                   with no host synchronisation per turn */
 } sw_precond_kind;
 
 typedef struct sw_model_s *sw_model;  /* opaque, owned by the library */

@@ -277,11 +277,8 @@ static cudaError_t conv_t(const ConvArgs &a, int sms, cudaStream_t s)
 {
     const int TW = a.W < 64 ? a.W : 64;
     const size_t smem = (size_t)(9 * COUT + (DGRAD ? 4 : 3) * (TW + 2)) * pitch(CIN) * 2;
-    cudaError_t e = cudaFuncSetAttribute(k_conv<CIN, COUT, DGRAD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
     int bps = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_conv<CIN, COUT, DGRAD>, 128, smem);
+    cudaError_t e = occupancy_once<k_conv<CIN, COUT, DGRAD>>(128, smem, &bps);
     if (e != cudaSuccess) return e;
     if (bps < 1) return cudaErrorInvalidConfiguration;
     const long ntiles = (long)a.B * a.H * (a.W / TW);

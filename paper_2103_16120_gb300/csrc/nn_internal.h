@@ -8,6 +8,40 @@
 
 namespace nn {
 
+// Resident blocks per SM of kernel KERN for a block size and a dynamic
+// shared-memory size, asked of the runtime once per (device, size) and kept,
+// with the kernel's shared-memory limit raised as needed (it only grows).
+// The network then launches the same way while a stream is being captured
+// into a graph (the learned preconditioner's device-side loop), where the
+// occupancy query may not run, and a launch recorded in a graph keeps a
+// limit large enough.
+template <auto KERN>
+inline cudaError_t occupancy_once(int threads, size_t smem, int *bps)
+{
+    struct Entry { int dev, threads; size_t smem; int bps; };
+    static Entry seen[16];
+    static int n = 0;
+    static size_t limit[8] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    for (int q = 0; q < n; ++q)
+        if (seen[q].dev == dev && seen[q].threads == threads && seen[q].smem == smem) {
+            *bps = seen[q].bps;
+            return cudaSuccess;
+        }
+    size_t &lim = limit[dev & 7];
+    if (smem > lim) {
+        e = cudaFuncSetAttribute(KERN, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        lim = smem;
+    }
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, KERN, threads, smem);
+    if (e != cudaSuccess) return e;
+    if (n < 16) seen[n++] = Entry{dev, threads, smem, *bps};
+    return cudaSuccess;
+}
+
 // 3x3 convolution over NHWC BF16 activations (see nn_conv.cu)
 struct ConvArgs {
     const __nv_bfloat16 *x;     // [B][H][W][cin]

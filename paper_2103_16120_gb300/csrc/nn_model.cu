@@ -307,6 +307,8 @@ float *model_scratch(sw_model_s *M, int ny, int nx)
     return M->A.ef;
 }
 
+const void *model_acts(sw_model_s *M) { return M->A.mem; }
+
 sw_status model_check_grid(const ::sw_grid_s *grid)
 {
     const GridView g = grid_view(grid);

@@ -316,11 +316,8 @@ template <int CIN, int COUT, bool DGRAD>
 static cudaError_t conv_tc_t(const ConvArgs &a, int sms, int *err, cudaStream_t s)
 {
     const size_t smem = tc_smem<CIN, COUT, DGRAD>();
-    cudaError_t e = cudaFuncSetAttribute(k_conv_tc<CIN, COUT, DGRAD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
     int bps = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_conv_tc<CIN, COUT, DGRAD>, 128, smem);
+    cudaError_t e = occupancy_once<k_conv_tc<CIN, COUT, DGRAD>>(128, smem, &bps);
     if (e != cudaSuccess) return e;
     if (bps < 1) return cudaErrorInvalidConfiguration;
     // TMEM: 512 columns per SM shared by the resident blocks

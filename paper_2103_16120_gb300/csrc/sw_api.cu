@@ -73,6 +73,11 @@ struct sw_grid_s {
     unsigned char *h_ring;
     cudaEvent_t ring_ev[4];
     int ring_next;
+    // the learned preconditioner's loop on the device (a CUDA graph with a
+    // conditional node) and what its nodes hold
+    cudaGraphExec_t lgraph;
+    unsigned long long lkey[14];
+    cudaStream_t lcap;             // a stream of its own to capture the loop on (not the legacy stream)
 };
 
 constexpr int RING = 4;
@@ -192,6 +197,8 @@ extern "C" sw_status sw_grid_destroy(sw_grid g)
     cudaFreeHost(g->h_mdev);
     cudaFreeHost(g->h_ring);
     for (int q = 0; q < RING; ++q) cudaEventDestroy(g->ring_ev[q]);
+    if (g->lgraph) cudaGraphExecDestroy(g->lgraph);
+    if (g->lcap) cudaStreamDestroy(g->lcap);
     delete g;
     return SW_OK;
 }
@@ -752,6 +759,8 @@ static sw_status solve_one_async(sw_grid g, const sw_solve_opts *o, const double
 }
 
 static sw_status finish_members(int n, const sw_grid *grids, sw_solve_stats *stats, cudaStream_t s);
+static sw_status build_learned_loop(sw_grid g, const sw_solve_opts *o, const Plan &P, int max_nx, const void *r,
+                                    float *ef, cudaStream_t s, cudaGraphExec_t *out);
 
 static sw_status solve_members(int n, const sw_grid *grids, const sw_solve_opts *o, const double *const *R,
                                double *const *phi, sw_solve_stats *stats, cudaStream_t s)
@@ -824,6 +833,27 @@ static sw_status solve_members(int n, const sw_grid *grids, const sw_solve_opts 
         float *ef = model_scratch(o->model, g->ny, g->nx);
         if (!ef) return fail(SW_ERR_OOM, "learned preconditioner: buffers");
         const void *r = (const char *)g->ws + ws_layout(g, o->prec, o->k).r;
+        // the turns run on the device, without a host round trip per turn:
+        // a graph whose conditional node repeats [network, e, resumed
+        // solve] while the member's state asks for a network turn
+        const unsigned long long key[14] = {
+            (unsigned long long)(uintptr_t)o->model, (unsigned long long)(uintptr_t)model_acts(o->model),
+            (unsigned long long)(uintptr_t)g->ws, (unsigned long long)(uintptr_t)ef, (unsigned long long)o->prec,
+            (unsigned long long)o->k, (unsigned long long)P.minb, (unsigned long long)P.warp,
+            (unsigned long long)grid, (unsigned long long)threads, (unsigned long long)smem,
+            (unsigned long long)max_nx, (unsigned long long)o->max_iters,
+            (unsigned long long)row_threads(g->nx, o->threads_per_row)};
+        if (std::memcmp(key, g->lkey, sizeof(key)) != 0) {
+            // (built once per configuration; one that cannot be built is not tried again)
+            if (g->lgraph) { cudaGraphExecDestroy(g->lgraph); g->lgraph = nullptr; }
+            if (build_learned_loop(g, o, P, max_nx, r, ef, s, &g->lgraph) != SW_OK) g->lgraph = nullptr;
+            std::memcpy(g->lkey, key, sizeof(key));
+        }
+        if (g->lgraph) {
+            CK(cudaGraphLaunch(g->lgraph, s));
+            return finish_members(n, grids, stats, s);
+        }
+        // (a graph that could not be built: the same turns driven by the host)
         for (int guard = 0; guard <= o->max_iters + 2; ++guard) {
             CK(cudaMemcpyAsync(g->h_ctl, &g->blk->ctl, sizeof(MemberCtl), cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
@@ -835,6 +865,83 @@ static sw_status solve_members(int n, const sw_grid *grids, const sw_solve_opts 
         }
     }
     return finish_members(n, grids, stats, s);
+}
+
+// the device-side loop of the learned preconditioner: its condition is set
+// by this kernel, which lets the body run while the member's state asks for a
+// network turn (at most limit turns; reset starts the count)
+__global__ void k_learned_cond(cudaGraphConditionalHandle h, SolverBlock *b, int limit, int reset)
+{
+    if (reset) b->lturns = 0;
+    const bool go = b->ctl.phase == PH_EXT && b->lturns < limit;
+    if (go) b->lturns += 1;
+    cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
+// Build the graph of the learned turns of one grid's solve: a first test of
+// the member's state, then a while node whose body runs the network on r,
+// stores its output as e, clears the barrier state, resumes the solver and
+// tests again.  The body is captured from the stream; nothing runs here.
+static sw_status build_learned_loop(sw_grid g, const sw_solve_opts *o, const Plan &P, int max_nx, const void *r,
+                                    float *ef, cudaStream_t s, cudaGraphExec_t *out)
+{
+    *out = nullptr;
+    // one application of the network outside the capture, so that the
+    // launchers' one-time queries (occupancy) are made (its output, in the
+    // scratch e, is overwritten by the loop's first turn)
+    if (model_precondition(o->model, g, r, o->prec == SW_PREC_FP64, ef, s) != SW_OK) return SW_ERR_CUDA;
+    // the body is captured on a stream of the grid's own (a capture cannot
+    // run on the legacy default stream); the graph is launched on s
+    if (!g->lcap && cudaStreamCreateWithFlags(&g->lcap, cudaStreamNonBlocking) != cudaSuccess) {
+        g->lcap = nullptr;
+        return SW_ERR_CUDA;
+    }
+    const cudaStream_t cs = g->lcap;
+    cudaGraph_t graph = nullptr;
+    if (cudaGraphCreate(&graph, 0) != cudaSuccess) return SW_ERR_CUDA;
+    sw_status st = SW_ERR_CUDA;
+    cudaGraphConditionalHandle h;
+    SolverBlock *b = g->blk;
+    int limit = o->max_iters + 2, reset = 1;
+    cudaGraphNode_t first = nullptr, loop = nullptr;
+    void *args[] = {(void *)&h, (void *)&b, (void *)&limit, (void *)&reset};
+    cudaKernelNodeParams kp = {};
+    kp.func = (void *)k_learned_cond;
+    kp.gridDim = dim3(1);
+    kp.blockDim = dim3(1);
+    kp.kernelParams = args;
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    if (cudaGraphConditionalHandleCreate(&h, graph, 0, 0) == cudaSuccess &&
+        cudaGraphAddKernelNode(&first, graph, nullptr, 0, &kp) == cudaSuccess) {
+        cp.conditional.handle = h;
+        if (cudaGraphAddNode(&loop, graph, &first, nullptr, 1, &cp) == cudaSuccess) {
+            cudaGraph_t body = cp.conditional.phGraph_out[0];
+            if (cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) == cudaSuccess) {
+                bool ok = model_precondition(o->model, g, r, o->prec == SW_PREC_FP64, ef, cs) == SW_OK;
+                ok = ok && launch_store_e(o->prec, g->blk->dev, ef, g->nx, g->ny, row_threads(g->nx, o->threads_per_row),
+                                          cs) == cudaSuccess;
+                ok = ok && cudaMemsetAsync(&g->blk->g, 0, sizeof(GlobalCtl), cs) == cudaSuccess;
+                ok = ok && launch_gcr(o->prec, o->k, P.minb, P.warp, g->desc, P.grid, max_nx, P.threads, P.smem, cs) ==
+                           cudaSuccess;
+                if (ok) {
+                    k_learned_cond<<<1, 1, 0, cs>>>(h, b, limit, 0);
+                    ok = cudaGetLastError() == cudaSuccess;
+                }
+                cudaGraph_t captured = nullptr;
+                const bool ended = cudaStreamEndCapture(cs, &captured) == cudaSuccess;
+                if (ok && ended && cudaGraphInstantiate(out, graph, 0) == cudaSuccess) st = SW_OK;
+            }
+        }
+    }
+    cudaGraphDestroy(graph);
+    if (st != SW_OK) {
+        *out = nullptr;
+        cudaGetLastError();         // the failed capture leaves no error behind: the host loop runs instead
+    }
+    return st;
 }
 
 // wait for a synchronous solve and fill the host stats from each member's

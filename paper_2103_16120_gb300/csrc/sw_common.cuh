@@ -156,6 +156,7 @@ struct alignas(256) SolverBlock {
                       ? sizeof(MemberDev<PolFP64>) : sizeof(MemberDev<PolF16>)];
     MemberCtl ctl;
     GlobalCtl g;
+    int lturns;                     // network turns of the device-side learned loop
 };
 
 // a one-member launch: the member and launch descriptors travel as kernel

@@ -72,6 +72,11 @@ size_t gcr_smem_bytes(int prec, int max_nx, int k, int cache_const, int cache_st
 // shared memory of the warp-per-row mode (0 when nx does not allow it)
 size_t gcr_warp_smem_bytes(int prec, int nx, int threads, int stage);
 cudaError_t gcr_occupancy(int prec, int k, int minb, int warp, int threads, size_t smem, int *blocks_per_sm);
+// Raise kernel f's dynamic shared-memory limit on the current device to at
+// least smem bytes.  The limit only grows: a launch recorded in a CUDA graph
+// (the ensemble and learned-preconditioner graphs) keeps its size, so a later
+// launch must not lower the limit below it.
+cudaError_t raise_smem_limit(const void *f, size_t smem);
 cudaError_t launch_gcr(int prec, int k, int minb, int warp, const EnsDesc *Ddev, int grid, int max_nx, int threads,
                        size_t smem, cudaStream_t s);
 // the instantiations of the GCR kernel, one translation unit each
@@ -114,6 +119,8 @@ sw_status model_precondition(::sw_model_s *m, const ::sw_grid_s *g, const void *
                              cudaStream_t s);
 sw_status model_check_grid(const ::sw_grid_s *g);
 float *model_scratch(::sw_model_s *m, int ny, int nx);
+// the model's activation storage (its address changes when it is reallocated)
+const void *model_acts(::sw_model_s *m);
 size_t member_dev_bytes(int prec);
 // set the calling thread's error message and return st (sw_api.cu)
 sw_status api_fail(sw_status st, const char *msg);

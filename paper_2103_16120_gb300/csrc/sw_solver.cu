@@ -282,12 +282,30 @@ static const void *gcr_kernel(int prec, int k, int minb, int warp)
     }
 }
 
+cudaError_t raise_smem_limit(const void *f, size_t smem)
+{
+    struct Lim { const void *f; int dev; size_t smem; };
+    static Lim lim[256];
+    static int n = 0;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    int q = 0;
+    while (q < n && !(lim[q].f == f && lim[q].dev == dev)) ++q;
+    if (q < n && lim[q].smem >= smem) return cudaSuccess;
+    e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (q < n) lim[q].smem = smem;
+    else if (n < 256) lim[n++] = Lim{f, dev, smem};
+    return cudaSuccess;
+}
+
 cudaError_t gcr_occupancy(int prec, int k, int minb, int warp, int threads, size_t smem, int *blocks_per_sm)
 {
     const void *f = gcr_kernel(prec, k, minb, warp);
     if (!f) return cudaErrorInvalidValue;
     if (smem > 227 * 1024 - 8192) { *blocks_per_sm = 0; return cudaSuccess; }
-    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = raise_smem_limit(f, smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, threads, smem);
 }
@@ -297,7 +315,7 @@ cudaError_t launch_gcr(int prec, int k, int minb, int warp, const EnsDesc *Ddev,
 {
     const void *f = gcr_kernel(prec, k, minb, warp);
     if (!f) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = raise_smem_limit(f, smem);
     if (e != cudaSuccess) return e;
     const EnsDesc *d = Ddev;
     int mx = max_nx;
