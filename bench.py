@@ -430,7 +430,7 @@ def run_gpu(args):
     # every step copies its coefficients and R from pinned host memory and
     # reads its solution back; the copies of step s + 1 run on a copy stream
     # into the second of two device buffer sets while step s solves
-    n_host = min(nsets, 50 if wl == "seq512" else 4)
+    n_host = min(nsets, 50 if wl == "seq512" else 10)   # one host set per timed step: no wrap of the sequence
     hcoef = [[torch.as_tensor(P[k]).pin_memory() for k in KEYS] for P in seq[:n_host]]
     hR = [torch.as_tensor(P["R"]).pin_memory() for P in seq[:n_host]]
     hphi = torch.zeros((ny, nx), dtype=torch.float64).pin_memory()
