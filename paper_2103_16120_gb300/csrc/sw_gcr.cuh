@@ -745,8 +745,10 @@ __global__ void __launch_bounds__(MAX_THREADS, MINB) k_gcr(const EnsDesc *__rest
             // the factors of the warp's first row for the next phase's zonal
             // solve, started now so that the copies overlap the member
             // barrier: a solve follows L(e) (the update), the update or the
-            // true residual or an earlier stage (a Richardson stage)
-            if (wf.lf && M.pc >= 3) {
+            // true residual or an earlier stage (a Richardson stage).  In the
+            // kernels specialised for one row length (the generic kernel,
+            // which runs the ensembles, measured slower with it)
+            if (WARP > 1 && wf.lf && M.pc >= 3) {
                 const int jf = wi * nb + local, ph = s_c.phase;
                 const bool next_solves = ph == PH_LE ||
                                          ((ph == PH_UB || ph == PH_TRUE || ph == PH_PREC0) && M.nstages > 1) ||
