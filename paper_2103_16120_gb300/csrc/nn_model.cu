@@ -51,7 +51,16 @@ struct sw_model_s {
     int *err;                    // device: a tensor-core wait ran out
     int t = 0;
     Acts A;
+    // a number no other model or activation storage of this process has had:
+    // a new one at creation and at every reallocation of the activations
+    unsigned long long gen = 0;
 };
+
+static unsigned long long next_model_gen()
+{
+    static unsigned long long n = 0;
+    return ++n;
+}
 
 namespace {
 
@@ -77,6 +86,7 @@ sw_status ensure_acts(sw_model_s *M, int B, int H, int W)
     Acts &A = M->A;
     if (A.mem && A.cap_n0 >= (size_t)B * H * W && A.cap_hw >= (size_t)H * W) return SW_OK;
     if (A.mem) { cudaFree(A.mem); A.mem = nullptr; }
+    M->gen = next_model_gen();
     const size_t N0 = (size_t)B * H * W, N1 = N0 / 4, N2 = N0 / 16;
     const size_t hb[] = {N0 * 16, N0 * 32, N1 * 32, N1 * 64, N2 * 64, N2 * 64, N1 * 128, N1 * 64, N0 * 96, N0 * 32,
                          N0 * 16, N0 * 32, N1 * 64, N2 * 64, N1 * 64, N0 * 32};
@@ -307,7 +317,7 @@ float *model_scratch(sw_model_s *M, int ny, int nx)
     return M->A.ef;
 }
 
-const void *model_acts(sw_model_s *M) { return M->A.mem; }
+unsigned long long model_gen(sw_model_s *M) { return M->gen; }
 
 sw_status model_check_grid(const ::sw_grid_s *grid)
 {
@@ -326,6 +336,7 @@ extern "C" sw_status sw_model_create(sw_model *out)
     if (param_count() != SW_MODEL_PARAMS) return sw::api_fail(SW_ERR_INTERNAL, "parameter count mismatch");
     sw_model_s *M = new (std::nothrow) sw_model_s();
     if (!M) return sw::api_fail(SW_ERR_OOM, "sw_model_create: host allocation failed");
+    M->gen = next_model_gen();
     cudaError_t e = cudaGetDevice(&M->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&M->sms, cudaDevAttrMultiProcessorCount, M->device);
     M->np = param_count();

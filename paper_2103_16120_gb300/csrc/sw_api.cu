@@ -837,7 +837,7 @@ static sw_status solve_members(int n, const sw_grid *grids, const sw_solve_opts 
         // a graph whose conditional node repeats [network, e, resumed
         // solve] while the member's state asks for a network turn
         const unsigned long long key[14] = {
-            (unsigned long long)(uintptr_t)o->model, (unsigned long long)(uintptr_t)model_acts(o->model),
+            (unsigned long long)(uintptr_t)o->model, model_gen(o->model),
             (unsigned long long)(uintptr_t)g->ws, (unsigned long long)(uintptr_t)ef, (unsigned long long)o->prec,
             (unsigned long long)o->k, (unsigned long long)P.minb, (unsigned long long)P.warp,
             (unsigned long long)grid, (unsigned long long)threads, (unsigned long long)smem,

@@ -119,8 +119,9 @@ sw_status model_precondition(::sw_model_s *m, const ::sw_grid_s *g, const void *
                              cudaStream_t s);
 sw_status model_check_grid(const ::sw_grid_s *g);
 float *model_scratch(::sw_model_s *m, int ny, int nx);
-// the model's activation storage (its address changes when it is reallocated)
-const void *model_acts(::sw_model_s *m);
+// a number that identifies the model and its current activation storage
+// (new for every model and at every reallocation of its activations)
+unsigned long long model_gen(::sw_model_s *m);
 size_t member_dev_bytes(int prec);
 // set the calling thread's error message and return st (sw_api.cu)
 sw_status api_fail(sw_status st, const char *msg);

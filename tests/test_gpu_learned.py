@@ -128,3 +128,28 @@ def test_learned_option_rejections():
     R96 = torch.as_tensor(P96["R"], device="cuda")
     with pytest.raises(sw.SwError):                 # grid the network cannot tile
         sw.sw_gcr_solve(g96, o, R96, torch.zeros_like(R96))
+
+
+def test_device_loop_follows_the_models_buffers():
+    """The learned turns run in a graph that the grid builds once and keeps.
+    When the model's activation storage is reallocated (here by a solve on a
+    larger grid), the next solve on the first grid rebuilds its graph: the
+    all-zero network still reproduces option 3 there, iterate for iterate."""
+    P = synth.problem(NX, NY, 7200)
+    g = grid_for(P)
+    R = torch.as_tensor(P["R"], device="cuda")
+    st3, phi3 = solve(g, R, prec=sw.SW_PREC_MIXED_FP16)
+    mz = model(np.zeros(sw.SW_MODEL_PARAMS))
+    st1, phi1 = solve(g, R, prec=sw.SW_PREC_MIXED_FP16, pc=sw.SW_PC_LEARNED, model=mz)
+    P2 = synth.problem(2 * NX, 2 * NY, 7201)
+    g2 = sw.sw_grid_create(2 * NX, 2 * NY)
+    sw.sw_elliptic_set_coeffs(g2, *[torch.as_tensor(P2[k], device="cuda") for k in sw.COEFF_KEYS])
+    st2, _ = solve(g2, torch.as_tensor(P2["R"], device="cuda"), prec=sw.SW_PREC_MIXED_FP16,
+                   pc=sw.SW_PC_LEARNED, model=mz)
+    assert st2.status == sw.SW_OK
+    for _ in range(2):
+        st, phi = solve(g, R, prec=sw.SW_PREC_MIXED_FP16, pc=sw.SW_PC_LEARNED, model=mz)
+        assert st.status == sw.SW_OK and st.iterations == st3.iterations == st1.iterations
+        assert st.fallbacks == st.iterations // 2
+        assert np.array_equal(phi, phi1)
+    assert np.linalg.norm(phi1 - phi3) <= 1e-12 * np.linalg.norm(phi3)
