@@ -647,6 +647,20 @@ __device__ void wphase_true(const MemberDev<Pol> &M, const RowView<Pol> &v, type
     wstage0_finish<Pol, SEL>(M, v, j, wb, w, f, staged);
 }
 
+// streaming store (evict-first) of 4 values: the update's p, L p and Phi,
+// which no phase reads again before the next update (measured 0.5 % faster at
+// 2048 x 1024 than plain stores)
+template <class T>
+__device__ __forceinline__ void stv4cs(T *p, const T (&v)[4])
+{
+    if constexpr (sizeof(T) == 4) {
+        __stcs((float4 *)p, make_float4(v[0], v[1], v[2], v[3]));
+    } else {
+        __stcs((double2 *)p, make_double2(v[0], v[1]));
+        __stcs((double2 *)p + 1, make_double2(v[2], v[3]));
+    }
+}
+
 template <class Pol, int KM>
 struct UbQuad {
     typename Pol::comp ev[4];
@@ -724,9 +738,9 @@ __device__ void wphase_ub(const MemberDev<Pol> &M, const MemberCtl &c, const Row
                 if (l < nd) part[2 + l] += la * (acc_t)d.lp4[l][u];
             wb[p0 + 33 * u] = stage0_input(M, v, eta, (comp)rs4[u], i0 + u);
         }
-        stv4(pn + i0, ps4);
-        stv4(Lpn + i0, ls4);
-        stv4(ph + i0, phn);
+        stv4cs(pn + i0, ps4);
+        stv4cs(Lpn + i0, ls4);
+        stv4cs(ph + i0, phn);
         stv4(v.r + i0, rs4);
     };
     quads<UbQuad<Pol, KM>>(nx, load, compute);
