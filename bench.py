@@ -73,7 +73,7 @@ SEQS = {
 # mixed-precision solver kernel per launch (seq512) or per GCR iteration
 # (seq2048, scaled by the launch's iterations); None until captured for the
 # current kernel
-TRAFFIC = {"seq512": None, "seq2048_per_iteration": 71.81e9 / 275}
+TRAFFIC = {"seq512": None, "seq2048_per_iteration": 70.40e9 / 275}
 
 
 def dist_env():
