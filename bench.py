@@ -633,8 +633,17 @@ def _grid(sw, torch, P, dev):
     return g
 
 
-def _time_solves(sw, torch, g, opts, Rs, reps):
-    """Mean solve time (CUDA events) and mean iterations over reps solves."""
+# kernels of one learned solve: the solver's first launch and the graph's first
+# test of the member's state, then per network turn the graph body's kernels
+# (sum of squares and features of r, input packing, 6 convolutions, 2 poolings,
+# 2 upsample + concatenations, output scaling, e stored in the member's format,
+# the resumed solver, the state test)
+LEARNED_LAUNCHES_PER_SOLVE, LEARNED_LAUNCHES_PER_TURN = 2, 17
+
+
+def _time_solves(sw, torch, g, opts, Rs, reps, turns=None):
+    """Mean solve time (CUDA events) and mean iterations over reps solves
+    (network turns of each solve appended to `turns` when given)."""
     stream = torch.cuda.current_stream()
     tot, its, fb = 0.0, 0, 0
     for q in range(reps):
@@ -650,6 +659,8 @@ def _time_solves(sw, torch, g, opts, Rs, reps):
         tot += a.elapsed_time(b)
         its += st.iterations
         fb += st.fallbacks
+        if turns is not None:
+            turns.append(st.network_turns)
     return tot / reps, its / reps, fb / reps
 
 
@@ -690,6 +701,7 @@ def run_learned(args):
     tflops = flops / (ms_step * 1e-3) / 1e12
     peak = _peaks().get("bf16_tflops", 1900.0)
     out = {}
+    turns = {(gx, tag): [] for gx in (256, 1024) for tag in ("option3", "learned")}
     for (gx, gy) in ((256, 128), (1024, 512)):
         Ps = [synth.problem(gx, gy, 4_000_000 + s) for s in range(2)]
         res = {}
@@ -700,9 +712,10 @@ def run_learned(args):
                 g = _grid(sw, torch, P, dev)
                 R = torch.as_tensor(P["R"], device=dev)
                 _time_solves(sw, torch, g, o, [R], 1)
-                a_, b_, c_ = _time_solves(sw, torch, g, o, [R], 3)
+                a_, b_, c_ = _time_solves(sw, torch, g, o, [R], 3, turns[(gx, tag)])
                 ms += a_ / len(Ps); its += b_ / len(Ps); fb += c_ / len(Ps)
-            res[tag] = {"solves_per_s": 1e3 / ms, "ms_per_solve": ms, "mean_iterations": its, "mean_fallbacks": fb}
+            res[tag] = {"solves_per_s": 1e3 / ms, "ms_per_solve": ms, "mean_iterations": its, "mean_fallbacks": fb,
+                        "mean_network_turns": sum(turns[(gx, tag)]) / len(turns[(gx, tag)])}
         out[f"{gx}x{gy}"] = res
     head = out["256x128"]["learned"]
     print(json.dumps({
@@ -722,7 +735,8 @@ def run_learned(args):
                      "peak_source": "measured bf16_tflops (of measured)"},
         "cpu_baseline": _oracle_baseline([synth.problem(256, 128, 4_000_000 + s_) for s_ in range(2)], 10.0,
                                          "FP64 oracle option-3 solves of the 256x128 evaluation problems"),
-        "gpu_launches": None,
+        # the headline's timed solves (the learned ones at 256 x 128)
+        "gpu_launches": sum(LEARNED_LAUNCHES_PER_SOLVE + LEARNED_LAUNCHES_PER_TURN * t for t in turns[(256, "learned")]),
         "clocks": clocks,
     }), flush=True)
 

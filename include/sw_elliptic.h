@@ -152,6 +152,8 @@ typedef struct {
     double true_rel_residual;      /* ||L(Phi) - R|| / ||R|| at exit, FP64 */
     double recursive_rel_residual; /* the GCR recursive residual at exit */
     double eta;                    /* eta used by option 3 */
+    int network_turns;             /* SW_PC_LEARNED: applications of the network (its
+                                    * proposed directions, fallbacks included); 0 otherwise */
 } sw_solve_stats;
 
 /* Fills *o with the defaults: k = 4, tol = 1e-8, max_iters = 1000,

@@ -48,7 +48,7 @@ class SolveStats(C.Structure):
     _fields_ = [("iterations", C.c_int), ("converged", C.c_int), ("status", C.c_int),
                 ("fallbacks", C.c_int), ("r0_norm", C.c_double), ("R_norm", C.c_double),
                 ("true_rel_residual", C.c_double), ("recursive_rel_residual", C.c_double),
-                ("eta", C.c_double)]
+                ("eta", C.c_double), ("network_turns", C.c_int)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -1,5 +1,6 @@
 // sw_api.cu -- the C ABI declared in include/sw_elliptic.h: grid handles,
 // coefficient storage, workspace, argument checks and kernel launches.
+#include <cstddef>
 #include <string>
 #include <cstdio>
 #include <cstring>
@@ -758,7 +759,8 @@ static sw_status solve_one_async(sw_grid g, const sw_solve_opts *o, const double
     return SW_OK;
 }
 
-static sw_status finish_members(int n, const sw_grid *grids, sw_solve_stats *stats, cudaStream_t s);
+static sw_status finish_members(int n, const sw_grid *grids, sw_solve_stats *stats, cudaStream_t s,
+                                bool learned = false);
 static sw_status build_learned_loop(sw_grid g, const sw_solve_opts *o, const Plan &P, int max_nx, const void *r,
                                     float *ef, cudaStream_t s, cudaGraphExec_t *out);
 
@@ -850,19 +852,25 @@ static sw_status solve_members(int n, const sw_grid *grids, const sw_solve_opts 
             std::memcpy(g->lkey, key, sizeof(key));
         }
         if (g->lgraph) {
+            // (the graph's state test counts the turns in the member's block)
             CK(cudaGraphLaunch(g->lgraph, s));
-            return finish_members(n, grids, stats, s);
+            return finish_members(n, grids, stats, s, true);
         }
         // (a graph that could not be built: the same turns driven by the host)
+        int turns = 0;
         for (int guard = 0; guard <= o->max_iters + 2; ++guard) {
             CK(cudaMemcpyAsync(g->h_ctl, &g->blk->ctl, sizeof(MemberCtl), cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
             if (g->h_ctl->phase != PH_EXT) break;
+            ++turns;
             if ((st = model_precondition(o->model, g, r, o->prec == SW_PREC_FP64, ef, s))) return st;
             CK(launch_store_e(o->prec, g->blk->dev, ef, g->nx, g->ny, row_threads(g->nx, o->threads_per_row), s));
             CK(cudaMemsetAsync(&g->blk->g, 0, sizeof(GlobalCtl), s));
             CK(launch_gcr(o->prec, o->k, P.minb, P.warp, lead->desc, grid, max_nx, threads, smem, s));
         }
+        CK(cudaMemcpyAsync(&g->blk->lturns, &turns, sizeof(int), cudaMemcpyHostToDevice, s));
+        CK(cudaStreamSynchronize(s));
+        return finish_members(n, grids, stats, s, true);
     }
     return finish_members(n, grids, stats, s);
 }
@@ -945,12 +953,17 @@ static sw_status build_learned_loop(sw_grid g, const sw_solve_opts *o, const Pla
 }
 
 // wait for a synchronous solve and fill the host stats from each member's
-// final state
-static sw_status finish_members(int n, const sw_grid *grids, sw_solve_stats *stats, cudaStream_t s)
+// final state (learned: also the network turns the member's block counted)
+static sw_status finish_members(int n, const sw_grid *grids, sw_solve_stats *stats, cudaStream_t s, bool learned)
 {
+    // the control words, the barrier state and the turn count lie together
+    constexpr size_t ctl_bytes = offsetof(SolverBlock, lturns) + sizeof(int) - offsetof(SolverBlock, ctl);
+    static_assert(offsetof(SolverBlock, g) - offsetof(SolverBlock, ctl) == sizeof(MemberCtl) &&
+                      ctl_bytes <= sizeof(MemberCtl) + sizeof(GlobalCtl) + 64,
+                  "the pinned control copy holds ctl, g and lturns in their device order");
     for (int m = 0; m < n; ++m) {
         sw_grid g = grids[m];
-        CK(cudaMemcpyAsync(g->h_ctl, &g->blk->ctl, sizeof(MemberCtl) + sizeof(GlobalCtl), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(g->h_ctl, &g->blk->ctl, ctl_bytes, cudaMemcpyDeviceToHost, s));
         CK(cudaMemcpyAsync(g->h_eta, g->eta, sizeof(double), cudaMemcpyDeviceToHost, s));
     }
     CK(cudaStreamSynchronize(s));
@@ -974,6 +987,9 @@ static sw_status finish_members(int n, const sw_grid *grids, sw_solve_stats *sta
             S.true_rel_residual = c.nR > 0 ? c.rn_true / c.nR : 0.0;
             S.recursive_rel_residual = c.nR > 0 ? std::sqrt(c.rn2_rec) / c.nR : 0.0;
             S.eta = *g->h_eta;
+            S.network_turns =
+                learned ? *(const int *)((const char *)g->h_ctl + offsetof(SolverBlock, lturns) - offsetof(SolverBlock, ctl))
+                        : 0;
         }
         if (mst != SW_OK && first == SW_OK) first = (sw_status)mst;
     }

@@ -64,6 +64,7 @@ def test_zero_network_reproduces_option3(prec):
     assert stl.status == st3.status == sw.SW_OK
     assert stl.iterations == st3.iterations
     assert stl.fallbacks == stl.iterations // 2          # every network turn
+    assert stl.network_turns == stl.fallbacks and st3.network_turns == 0
     assert np.linalg.norm(phil - phi3) <= 1e-12 * np.linalg.norm(phi3)
 
 
@@ -105,6 +106,7 @@ def test_learned_solve_converges_to_the_oracle_solution(trained, prec):
         print(f"prec {prec} seed {s}: option 3 {st3.iterations} its; learned {st.iterations} its, "
               f"{st.fallbacks} fallbacks, error {err:.2e}")
         assert st.status == sw.SW_OK and st.true_rel_residual <= 1e-8
+        assert st.fallbacks <= st.network_turns <= (st.iterations + 1) // 2
         assert err <= 1e-6
         assert st.iterations <= 2 * st3.iterations
 
@@ -150,6 +152,6 @@ def test_device_loop_follows_the_models_buffers():
     for _ in range(2):
         st, phi = solve(g, R, prec=sw.SW_PREC_MIXED_FP16, pc=sw.SW_PC_LEARNED, model=mz)
         assert st.status == sw.SW_OK and st.iterations == st3.iterations == st1.iterations
-        assert st.fallbacks == st.iterations // 2
+        assert st.fallbacks == st.network_turns == st.iterations // 2
         assert np.array_equal(phi, phi1)
     assert np.linalg.norm(phi1 - phi3) <= 1e-12 * np.linalg.norm(phi3)
