@@ -735,7 +735,7 @@ __global__ void __launch_bounds__(MAX_THREADS, MINB) k_gcr(const EnsDesc *__rest
                 case PH_UB: wphase_ub<Pol, KM, SEL>(M, s_c, v, eta, j, wb, wr, wf, part); break;
                 case PH_PREC: wprecond_stage<Pol, SEL>(M, v, eta, s_c.stage, j, wb, wr, wf); break;
                 case PH_PREC0: wphase_prec0<Pol, SEL>(M, v, eta, j, wb, wr, wf); break;
-                case PH_LE: wphase_le<Pol, KM>(M, s_c, v, j, wr, part); break;
+                case PH_LE: wphase_le<Pol, KM, SEL>(M, s_c, v, j, wr, part); break;
                 case PH_ZERO:
                     for (int i = threadIdx.x & 31; i < nx; i += 32) M.phi[(size_t)j * nx + i] = 0.0;
                     break;

@@ -18,6 +18,8 @@
 // path (sw_rows.cuh, sw_solver.cu): the same expressions in the same order.
 #pragma once
 
+#include <type_traits>
+
 #include "sw_rows.cuh"
 
 namespace sw {
@@ -107,6 +109,26 @@ __device__ __forceinline__ void q6(const QRow<Pol> &q, int i0, int nx, typename 
     if constexpr (!Pol::kMixed) cg6(q.h, a, nx, v);
     else if (q.band) cg6(q.f, a, nx, v);
     else cg6h(q.h, a, nx, q.sc, v);
+}
+
+// q6 for a row inside the grid, unshifted and outside the FP32 pole band
+template <class Pol>
+__device__ __forceinline__ void q6i(const QRow<Pol> &q, int i0, int nx, typename Pol::comp (&v)[6])
+{
+    if constexpr (!Pol::kMixed) cg6(q.h, i0, nx, v);
+    else cg6h(q.h, i0, nx, q.sc, v);
+}
+
+// a row whose three source rows are all plain (q6i applies): the stencil
+// passes of the generic warp kernels take a loop with these conditions fixed
+// at compile time, whose loads are then free of per-row branches (the
+// kernels specialised for one row length keep the single loop: their larger
+// code measured slower with two)
+template <class Pol>
+__device__ __forceinline__ bool rows_plain(const QRow<Pol> &s, const QRow<Pol> &x, const QRow<Pol> &n, bool has_n,
+                                           bool has_s)
+{
+    return has_n && has_s && !s.band && !x.band && !n.band && s.sh == 0 && n.sh == 0;
 }
 
 // 4 values i0 .. i0 + 3 of the row's own preconditioner output (q_load)
@@ -775,32 +797,49 @@ __device__ void wprecond_stage(const MemberDev<Pol> &M, const RowView<Pol> &v, t
     float *os = last ? M.e_s : ((mu & 1) ? M.qb_s : M.qa_s);
     const QRow<Pol> qS = qrow(M, ih, if32, is, j - 1), qX = qrow(M, ih, if32, is, j), qN = qrow(M, ih, if32, is, j + 1);
     const RowCoef<CT> c = coef_of(v);
-    auto load = [&](int i0, StQuad<Pol> &d) {
-        q6(qX, i0, nx, d.xc);
-        q6(qN, i0, nx, d.xn);
-        q6(qS, i0, nx, d.xs);
-        coef4(c, i0, nx, !opt3, has_n, has_s, d.k);
-        ldv4(v.r + i0, d.rv);
+    // PL: option 3 on a plain row (rows_plain), conditions fixed at compile time
+    auto pass = [&](auto plain_t) {
+        constexpr bool PL = decltype(plain_t)::value;
+        const bool o3 = PL || opt3, hn = PL || has_n, hs = PL || has_s;
+        auto load = [&](int i0, StQuad<Pol> &d) {
+            if constexpr (PL) {
+                q6i(qX, i0, nx, d.xc);
+                q6i(qN, i0, nx, d.xn);
+                q6i(qS, i0, nx, d.xs);
+            } else {
+                q6(qX, i0, nx, d.xc);
+                q6(qN, i0, nx, d.xn);
+                q6(qS, i0, nx, d.xs);
+            }
+            coef4(c, i0, nx, !o3, hn, hs, d.k);
+            ldv4(v.r + i0, d.rv);
 #pragma unroll
-        for (int u = 0; u < 4; ++u) d.dg[u] = comp(1);
-        if (!opt3) {
-            CT d4[4];
-            ldg4(v.diag + i0, d4);
+            for (int u = 0; u < 4; ++u) d.dg[u] = comp(1);
+            if (!o3) {
+                CT d4[4];
+                ldg4(v.diag + i0, d4);
 #pragma unroll
-            for (int u = 0; u < 4; ++u) d.dg[u] = (comp)d4[u];
-        }
+                for (int u = 0; u < 4; ++u) d.dg[u] = (comp)d4[u];
+            }
+        };
+        auto compute = [&](int i0, StQuad<Pol> &d) {
+            comp y[4];
+            apply4(d.k, d.xc, d.xn, d.xs, hn, hs, y);
+            const int p0 = tpos4(w, i0);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const comp xv = d.xc[u + 1];
+                wb[p0 + 33 * u] = o3 ? xv + eta * (y[u] - d.rv[u]) : xv + (comp)M.omega * (d.rv[u] - y[u]) / d.dg[u];
+            }
+        };
+        quads<StQuad<Pol>>(nx, load, compute);
     };
-    auto compute = [&](int i0, StQuad<Pol> &d) {
-        comp y[4];
-        apply4(d.k, d.xc, d.xn, d.xs, has_n, has_s, y);
-        const int p0 = tpos4(w, i0);
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const comp xv = d.xc[u + 1];
-            wb[p0 + 33 * u] = opt3 ? xv + eta * (y[u] - d.rv[u]) : xv + (comp)M.omega * (d.rv[u] - y[u]) / d.dg[u];
-        }
-    };
-    quads<StQuad<Pol>>(nx, load, compute);
+    if constexpr (SEL < 0) {
+        if (opt3 && rows_plain(qS, qX, qN, has_n, has_s)) pass(std::true_type{});
+        else pass(std::false_type{});
+    } else {
+        pass(std::false_type{});
+    }
     __syncwarp();
     SW_TRACE(311);
     float lmax = -1.f;
@@ -822,7 +861,7 @@ struct LeQuad {
 
 // L(e) of row j into the row's L e and the inner products <Le,Le>, <r,Le>,
 // <Le,Lp_l>, <r,Lp_l> (phase_le)
-template <class Pol, int KM>
+template <class Pol, int KM, int SEL>
 __device__ void wphase_le(const MemberDev<Pol> &M, const MemberCtl &c, const RowView<Pol> &v, int j, const WRow w,
                           typename Acc<Pol>::type (&part)[2 + 2 * KM])
 {
@@ -839,38 +878,55 @@ __device__ void wphase_le(const MemberDev<Pol> &M, const MemberCtl &c, const Row
     const vec *Lpl[KM];
 #pragma unroll
     for (int l = 0; l < KM; ++l) Lpl[l] = v.Lpb + (size_t)phys_slot(c, M.k, l < nd ? l : 0) * v.vstride;
-    auto load = [&](int i0, LeQuad<Pol, KM> &d) {
-        q6(qX, i0, nx, d.xc);
-        q6(qN, i0, nx, d.xn);
-        q6(qS, i0, nx, d.xs);
-        coef4(cf, i0, nx, true, has_n, has_s, d.k);
-        ldv4(v.r + i0, d.r4);
+    // PL: a plain row (rows_plain), conditions fixed at compile time
+    auto pass = [&](auto plain_t) {
+        constexpr bool PL = decltype(plain_t)::value;
+        const bool hn = PL || has_n, hs = PL || has_s;
+        auto load = [&](int i0, LeQuad<Pol, KM> &d) {
+            if constexpr (PL) {
+                q6i(qX, i0, nx, d.xc);
+                q6i(qN, i0, nx, d.xn);
+                q6i(qS, i0, nx, d.xs);
+            } else {
+                q6(qX, i0, nx, d.xc);
+                q6(qN, i0, nx, d.xn);
+                q6(qS, i0, nx, d.xs);
+            }
+            coef4(cf, i0, nx, true, hn, hs, d.k);
+            ldv4(v.r + i0, d.r4);
 #pragma unroll
-        for (int l = 0; l < KM; ++l)
-            if (l < nd) ldv4(Lpl[l] + i0, d.lp4[l]);
-    };
-    auto compute = [&](int i0, LeQuad<Pol, KM> &d) {
-        comp y[4];
-        apply4(d.k, d.xc, d.xn, d.xs, has_n, has_s, y);
-        vec le4[4];
+            for (int l = 0; l < KM; ++l)
+                if (l < nd) ldv4(Lpl[l] + i0, d.lp4[l]);
+        };
+        auto compute = [&](int i0, LeQuad<Pol, KM> &d) {
+            comp y[4];
+            apply4(d.k, d.xc, d.xn, d.xs, hn, hs, y);
+            vec le4[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) le4[u] = (vec)y[u];
-        stv4(v.Le + i0, le4);
+            for (int u = 0; u < 4; ++u) le4[u] = (vec)y[u];
+            stv4(v.Le + i0, le4);
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const acc_t la = (acc_t)le4[u], rv = (acc_t)d.r4[u];
-            part[0] += la * la;
-            part[1] += rv * la;
+            for (int u = 0; u < 4; ++u) {
+                const acc_t la = (acc_t)le4[u], rv = (acc_t)d.r4[u];
+                part[0] += la * la;
+                part[1] += rv * la;
 #pragma unroll
-            for (int l = 0; l < KM; ++l) {
-                if (l < nd) {
-                    part[2 + l] += la * (acc_t)d.lp4[l][u];
-                    part[2 + KM + l] += rv * (acc_t)d.lp4[l][u];
+                for (int l = 0; l < KM; ++l) {
+                    if (l < nd) {
+                        part[2 + l] += la * (acc_t)d.lp4[l][u];
+                        part[2 + KM + l] += rv * (acc_t)d.lp4[l][u];
+                    }
                 }
             }
-        }
+        };
+        quads<LeQuad<Pol, KM>>(nx, load, compute);
     };
-    quads<LeQuad<Pol, KM>>(nx, load, compute);
+    if constexpr (SEL < 0) {
+        if (rows_plain(qS, qX, qN, has_n, has_s)) pass(std::true_type{});
+        else pass(std::false_type{});
+    } else {
+        pass(std::false_type{});
+    }
     SW_TRACE(111);
 }
 
