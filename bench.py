@@ -831,7 +831,8 @@ def run_ensemble(args):
                      "note": "algorithmic bytes (172 B per point per iteration) / ensemble time",
                      "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
         "cpu_baseline": _oracle_baseline(Ps, 15.0, "FP64 oracle solves of the ensemble members one after another"),
-        "gpu_launches": 1 * args.steps,
+        # per replay: the members' initial state (k_init_members) and the solve (k_gcr)
+        "gpu_launches": 2 * args.steps,
         "clocks": clocks,
     }), flush=True)
 
